@@ -1,0 +1,157 @@
+"""The workload configurations as seeded synthetic instances.
+
+config0: n = 512, upper triangular T with 64 prescribed eigenvalues evenly
+         spaced in [-64, 64] and 448 more evenly spaced in [-512, 512] with
+         U(-0.1, 0.1) jitter, strictly upper entries N(0,1); A = Q T Q^T with a
+         Haar Q, reduced to Hessenberg H.  64 real shifts equal to the
+         prescribed eigenvalues; unit-norm N(0,1) starting vectors.
+config1: n = 4096, quasi-triangular T with 1024 real eigenvalues U[-n, n] and
+         1536 blocks [[a, b], [-b, a]], a ~ U[-n, n], b ~ U[0.5, 2].
+         512 real + 256 complex shifts (one member of each conjugate pair),
+         drawn from the prescribed eigenvalues, in a seeded mixed order.
+config2: n = 8192, real eigenvalues U[-n, n] with minimum gap >= 1e-2, 2048
+         real shifts.
+small_instance: the config1 recipe at any size, for parity tests.
+
+Layout conventions (those of the C ABI): H, Q0 and B are column-major; a real
+shift owns one column of B and X, a complex shift two adjacent columns
+[re, im]; shifts are given as (wr, wi) with wi != 0 marking a complex shift.
+"""
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from .matrices import (S_B, S_EIG, S_IMAG, S_JIT, S_SHIFT, haar_orthogonal, hessenberg_reduce,
+                       quasi_triangular)
+from .rng import uniform
+
+
+@dataclass
+class Instance:
+    name: str
+    n: int
+    H: np.ndarray
+    Q0: np.ndarray
+    wr: np.ndarray
+    wi: np.ndarray
+    B: np.ndarray
+    A: Optional[np.ndarray] = None
+    eigs: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.complex128))
+
+    @property
+    def m(self):
+        return len(self.wr)
+
+    @property
+    def m_cplx(self):
+        return int(np.count_nonzero(self.wi))
+
+    @property
+    def m_real(self):
+        return self.m - self.m_cplx
+
+    @property
+    def ncol(self):
+        return self.m_real + 2 * self.m_cplx
+
+
+def column_offsets(wi):
+    """Column of each shift in B/X: real shifts own one column, complex two."""
+    widths = np.where(np.asarray(wi) != 0.0, 2, 1)
+    return np.concatenate([[0], np.cumsum(widths)]).astype(np.int64)
+
+
+def _starting_vectors(n, wi, seed):
+    """Unit-2-norm N(0,1) starting vectors; a complex shift's [re, im] pair is
+    normalized as one complex vector."""
+    offs = column_offsets(wi)
+    ncol = int(offs[-1])
+    from .rng import normal
+    B = normal(seed, S_B, n * ncol).reshape(n, ncol, order="F")
+    for l in range(len(wi)):
+        c0, c1 = offs[l], offs[l + 1]
+        B[:, c0:c1] /= np.linalg.norm(B[:, c0:c1])
+    return np.asfortranarray(B)
+
+
+def _build(name, n, T, seed, wr, wi, keep_a):
+    Q = haar_orthogonal(n, seed)
+    A = np.asfortranarray(Q @ T @ Q.T)
+    H, Q0 = hessenberg_reduce(A)
+    B = _starting_vectors(n, wi, seed)
+    return Instance(name=name, n=n, H=H, Q0=Q0, wr=np.asarray(wr, dtype=np.float64),
+                    wi=np.asarray(wi, dtype=np.float64), B=B, A=A if keep_a else None)
+
+
+def config0(seed=0, keep_a=False):
+    n = 512
+    pres = np.linspace(-64.0, 64.0, 64)
+    rest = np.linspace(-512.0, 512.0, 448) + uniform(seed, S_JIT, 448, -0.1, 0.1)
+    eigs = np.concatenate([pres, rest])
+    T, _ = quasi_triangular(n, eigs, [], seed)
+    inst = _build("config0", n, T, seed, pres, np.zeros(64), keep_a)
+    inst.eigs = eigs.astype(np.complex128)
+    return inst
+
+
+def _mixed_instance(name, n, n_real_eigs, m_real, m_cplx, seed, keep_a, real_lo=None):
+    n_pairs = (n - n_real_eigs) // 2
+    assert n_real_eigs + 2 * n_pairs == n
+    lo = -float(n) if real_lo is None else real_lo
+    reals = uniform(seed, S_EIG, n_real_eigs, lo, float(n))
+    a = uniform(seed, S_EIG, n_pairs, -float(n), float(n), start=n_real_eigs)
+    b = uniform(seed, S_IMAG, n_pairs, 0.5, 2.0)
+    T, _ = quasi_triangular(n, reals, list(zip(a, b)), seed)
+    # shifts: m_real real eigenvalues and m_cplx pairs, in a seeded mixed order
+    pick_r = np.argsort(uniform(seed, S_SHIFT, n_real_eigs), kind="stable")[:m_real]
+    pick_c = np.argsort(uniform(seed, S_SHIFT, max(n_pairs, 1), start=n_real_eigs),
+                        kind="stable")[:m_cplx]
+    wr = np.concatenate([reals[pick_r], a[pick_c]])
+    wi = np.concatenate([np.zeros(m_real), b[pick_c]])
+    order = np.argsort(uniform(seed, S_SHIFT, m_real + m_cplx, start=3 * n), kind="stable")
+    wr, wi = wr[order], wi[order]
+    inst = _build(name, n, T, seed, wr, wi, keep_a)
+    inst.eigs = np.concatenate([reals, a + 1j * b, a - 1j * b])
+    return inst
+
+
+def config1(seed=1, keep_a=False):
+    return _mixed_instance("config1", 4096, 1024, 512, 256, seed, keep_a)
+
+
+def _gapped_uniform(n, lo, hi, gap, seed):
+    """n values uniform in [lo, hi) whose sorted neighbours differ by >= gap:
+    offending values are redrawn from fresh counter indices until none is left."""
+    vals = uniform(seed, S_EIG, n, lo, hi)
+    nxt = n
+    while True:
+        order = np.argsort(vals, kind="stable")
+        s = vals[order]
+        bad = np.nonzero(np.diff(s) < gap)[0]
+        if len(bad) == 0:
+            return vals
+        idx = order[bad + 1]
+        vals[idx] = uniform(seed, S_EIG, len(idx), lo, hi, start=nxt)
+        nxt += len(idx)
+
+
+def config2(seed=2, keep_a=False):
+    n = 8192
+    eigs = _gapped_uniform(n, -float(n), float(n), 1e-2, seed)
+    T, _ = quasi_triangular(n, eigs, [], seed)
+    pick = np.argsort(uniform(seed, S_SHIFT, n), kind="stable")[:2048]
+    inst = _build("config2", n, T, seed, eigs[pick], np.zeros(2048), keep_a)
+    inst.eigs = eigs.astype(np.complex128)
+    return inst
+
+
+def small_instance(n, m_real, m_cplx, seed, keep_a=False):
+    """The config1 recipe at size n: about n/4 real eigenvalues, the rest in
+    complex pairs; m_real real and m_cplx complex shifts in mixed order."""
+    n_real = max(m_real, n // 4)
+    if (n - n_real) % 2:
+        n_real += 1
+    n_pairs = (n - n_real) // 2
+    assert m_cplx <= n_pairs and m_real <= n_real
+    return _mixed_instance("small_n%d" % n, n, n_real, m_real, m_cplx, seed, keep_a)

@@ -1,0 +1,191 @@
+"""FP64 CPU oracle for the robust multi-shift shifted-Hessenberg solve.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may use this package; the product path never
+does.  It is an independent restatement of the method (Henry's RQ algorithm,
+Alg. "henry", with the robust scaling of Sec. 4.1 and the normalization and
+backtransform of Alg. "consistency-scaling"), written in plain C in
+``hsein_oracle.c`` and wrapped here with ctypes.  It shares no code with the
+CUDA library.
+
+Every function here is pinned by tests against values that do not come from
+the oracle itself (exact rational solves, closed-form eigenvectors, the
+paper's printed 6x6 example, invariants); see tests/test_oracle_*.py.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+LOG2_OMEGA_DEFAULT = 1000.0
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(_build.build()))
+    return _lib
+
+
+def swap_library(path):
+    """Load the oracle from another build of hsein_oracle.c (used by the
+    mutation tests to check that the pins reject planted mistakes).  Returns
+    the previously loaded library handle; pass it back to restore."""
+    global _lib
+    old = _load()
+    _lib = path if isinstance(path, ctypes.CDLL) else _bind(ctypes.CDLL(path))
+    return old
+
+
+def _bind(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.oracle_hnorm_inf.restype = ctypes.c_double
+    lib.oracle_hnorm_inf.argtypes = [ctypes.c_int, dp, ctypes.c_int]
+    lib.oracle_henry_real.restype = ctypes.c_int
+    lib.oracle_henry_real.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, dp,
+                                      ctypes.c_double, ctypes.c_int, dp, ip, dp, dp, dp]
+    lib.oracle_henry_cplx.restype = ctypes.c_int
+    lib.oracle_henry_cplx.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, dp, ctypes.c_double, ctypes.c_int,
+                                      dp, ip, dp, dp, dp]
+    lib.oracle_backtransform_real.restype = None
+    lib.oracle_backtransform_real.argtypes = [ctypes.c_int, dp, dp, dp]
+    lib.oracle_backtransform_cplx.restype = None
+    lib.oracle_backtransform_cplx.argtypes = [ctypes.c_int, dp, dp, dp]
+    lib.oracle_hsein.restype = ctypes.c_int
+    lib.oracle_hsein.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                 ctypes.c_int, dp, ctypes.c_int, ip, ip, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_int]
+    lib.oracle_q0_apply.restype = None
+    lib.oracle_q0_apply.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
+                                    ctypes.c_int, dp, ctypes.c_int, ctypes.c_int]
+    lib.oracle_gehrd.restype = None
+    lib.oracle_gehrd.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int, dp,
+                                 ctypes.c_int, dp]
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a):
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def hnorm_inf(H):
+    """||H||_inf of an upper Hessenberg matrix (max absolute row sum)."""
+    H = _f64(H)
+    return _load().oracle_hnorm_inf(H.shape[0], _dp(H), H.shape[0])
+
+
+def henry_real(H, lam, b, log2_omega=LOG2_OMEGA_DEFAULT, robust=True):
+    """One real-shift Henry solve.  Returns (x, e, C, S, replaced) with the
+    true solution of (H - lam I) x = b equal to x * 2**e."""
+    H = _f64(H)
+    n = H.shape[0]
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty(n); C = np.empty(n); S = np.empty(n); work = np.empty(2 * n)
+    e = np.zeros(1, dtype=np.int32)
+    rep = _load().oracle_henry_real(n, _dp(H), n, float(lam), _dp(b), float(log2_omega),
+                                    int(bool(robust)), _dp(x), _ip(e), _dp(C), _dp(S), _dp(work))
+    return x, int(e[0]), C, S, bool(rep)
+
+
+def henry_cplx(H, lam, b, log2_omega=LOG2_OMEGA_DEFAULT, robust=True):
+    """One complex-shift Henry solve (lam complex, b complex).  Returns
+    (x, e, C, S, replaced), C complex, S real."""
+    H = _f64(H)
+    n = H.shape[0]
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    x = np.empty(n, dtype=np.complex128); C = np.empty(n, dtype=np.complex128)
+    S = np.empty(n); work = np.empty(2 * n, dtype=np.complex128)
+    e = np.zeros(1, dtype=np.int32)
+    lam = complex(lam)
+    rep = _load().oracle_henry_cplx(n, _dp(H), n, lam.real, lam.imag, _dp(b.view(np.float64)),
+                                    float(log2_omega), int(bool(robust)),
+                                    _dp(x.view(np.float64)), _ip(e),
+                                    _dp(C.view(np.float64)), _dp(S),
+                                    _dp(work.view(np.float64)))
+    return x, int(e[0]), C, S, bool(rep)
+
+
+def backtransform_real(C, S, x):
+    x = np.array(x, dtype=np.float64)
+    _load().oracle_backtransform_real(len(x), _dp(np.ascontiguousarray(C, dtype=np.float64)),
+                                      _dp(np.ascontiguousarray(S, dtype=np.float64)), _dp(x))
+    return x
+
+
+def backtransform_cplx(C, S, x):
+    x = np.array(x, dtype=np.complex128)
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    _load().oracle_backtransform_cplx(len(x), _dp(C.view(np.float64)),
+                                      _dp(np.ascontiguousarray(S, dtype=np.float64)),
+                                      _dp(x.view(np.float64)))
+    return x
+
+
+def column_offsets(wi):
+    """Column of each shift in B/X: real shifts own one column, complex two."""
+    wi = np.asarray(wi, dtype=np.float64)
+    widths = np.where(wi != 0.0, 2, 1)
+    return np.concatenate([[0], np.cumsum(widths)]).astype(np.int64)
+
+
+def hsein(H, wr, wi, B=None, log2_omega=LOG2_OMEGA_DEFAULT, robust=True, nthreads=0,
+          return_exponents=False):
+    """Unit-norm eigenvector approximations for every shift (Henry + scaling +
+    normalization + backtransform + Varah's convergence test).  Returns
+    (X, status) with X of shape (n, ncol); complex shifts own [re, im]."""
+    H = _f64(H)
+    n = H.shape[0]
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    wi = np.ascontiguousarray(wi, dtype=np.float64)
+    m = len(wr)
+    ncol = int(column_offsets(wi)[-1])
+    X = np.zeros((n, ncol), order="F")
+    status = np.zeros(m, dtype=np.int32)
+    exps = np.zeros(m, dtype=np.int32)
+    if B is None:
+        bptr, ldb = None, n
+    else:
+        B = _f64(B)
+        assert B.shape == (n, ncol)
+        bptr, ldb = _dp(B), n
+    rc = _load().oracle_hsein(n, _dp(H), n, m, _dp(wr), _dp(wi), bptr, ldb, _dp(X), n,
+                              _ip(status), _ip(exps), float(log2_omega), int(bool(robust)),
+                              int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle_hsein failed to allocate")
+    if return_exponents:
+        return X, status, exps
+    return X, status
+
+
+def q0_apply(Q, X, nthreads=0):
+    """Z = Q X column by column (plain loops)."""
+    Q = _f64(Q)
+    X = _f64(X)
+    n, ncol = X.shape
+    Z = np.zeros((n, ncol), order="F")
+    _load().oracle_q0_apply(n, _dp(Q), n, ncol, _dp(X), n, _dp(Z), n, int(nthreads))
+    return Z
+
+
+def gehrd(A):
+    """Plain Householder reduction A = Q H Q^T.  Returns (H, Q)."""
+    A = _f64(A)
+    n = A.shape[0]
+    H = np.zeros((n, n), order="F"); Q = np.zeros((n, n), order="F")
+    work = np.empty(2 * n)
+    _load().oracle_gehrd(n, _dp(A), n, _dp(H), n, _dp(Q), n, _dp(work))
+    return H, Q

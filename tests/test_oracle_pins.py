@@ -1,0 +1,367 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself.
+
+Each test checks the oracle against one of: an exact rational solve of the
+same system, a closed-form eigenvector, the matrices the paper prints for its
+second test problem (Sec. 5.2), properties the paper states (unit norm after
+the backtransform, c^2 + s^2 = 1, the padding rotation, the triangular factor
+(H - lambda I) G_n^T ... G_2^T = R of Sec. 3.1, the "good" system never
+scaling and the "bad" one scaling), a library routine, or the normwise
+residual bound 100 n eps.
+"""
+import numpy as np
+import pytest
+
+import hsein_inputs as hi
+import oracle
+from tests.exact import exact_solve, read_golden_blocks
+from tests.metrics import EPS, angle, as_vectors, residual, residuals
+
+import os
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def random_hessenberg(n, seed, scale=1.0):
+    H = hi.normal(seed, 50, n * n).reshape(n, n, order="F") * scale
+    return np.asfortranarray(np.triu(H, -1))
+
+
+def solve_oracle_real(H, lam, b, **kw):
+    x, e, C, S, rep = oracle.henry_real(H, lam, b, **kw)
+    return oracle.backtransform_real(C, S, x) * 2.0 ** e
+
+
+def solve_oracle_cplx(H, lam, b, **kw):
+    x, e, C, S, rep = oracle.henry_cplx(H, lam, b, **kw)
+    return oracle.backtransform_cplx(C, S, x) * 2.0 ** e
+
+
+# ------------------------------------------------------------ exact solves
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_real_solve_matches_exact_rational(n, seed):
+    H = random_hessenberg(n, seed)
+    b = hi.normal(seed, 51, n)
+    lam = float(hi.uniform(seed, 52, 1, -2.0, 2.0)[0])
+    x = solve_oracle_real(H, lam, b)
+    xe = exact_solve(H, lam, b).real
+    kappa = np.linalg.cond(H - lam * np.eye(n))
+    err = np.linalg.norm(x - xe) / np.linalg.norm(xe)
+    assert err <= 4 * n * kappa * EPS, (err, kappa)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 12])
+@pytest.mark.parametrize("seed", [4, 5])
+def test_complex_solve_matches_exact_rational(n, seed):
+    H = random_hessenberg(n, seed)
+    b = hi.normal(seed, 51, n) + 1j * hi.normal(seed, 53, n)
+    lam = complex(hi.uniform(seed, 52, 1, -2.0, 2.0)[0], hi.uniform(seed, 54, 1, 0.1, 2.0)[0])
+    x = solve_oracle_cplx(H, lam, b)
+    xe = exact_solve(H, lam, b)
+    kappa = np.linalg.cond(H - lam * np.eye(n))
+    err = np.linalg.norm(x - xe) / np.linalg.norm(xe)
+    assert err <= 4 * n * kappa * EPS, (err, kappa)
+
+
+@pytest.mark.parametrize("n", [4, 9])
+def test_far_shift_is_well_conditioned_to_1e13(n):
+    # a shift outside the spectrum: the system is well conditioned and the
+    # oracle must agree with the exact solution to 1e-13
+    H = random_hessenberg(n, 7)
+    lam = 10.0 * np.abs(H).sum(axis=1).max()
+    b = hi.normal(7, 51, n)
+    x = solve_oracle_real(H, lam, b)
+    xe = exact_solve(H, lam, b).real
+    assert np.linalg.norm(x - xe) <= 1e-13 * np.linalg.norm(xe)
+    xc = solve_oracle_cplx(H, complex(lam, 1.0), b.astype(complex))
+    xce = exact_solve(H, complex(lam, 1.0), b)
+    assert np.linalg.norm(xc - xce) <= 1e-13 * np.linalg.norm(xce)
+
+
+# --------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_companion_eigenvectors_closed_form(n):
+    roots = np.arange(1, n + 1, dtype=np.float64)
+    C = hi.companion(roots)
+    wr = roots.copy()
+    wi = np.zeros(n)
+    X, status = oracle.hsein(C, wr, wi, B=hi.unit_columns(n, n, seed=n))
+    assert np.all(status == 0)
+    for l, r in enumerate(roots):
+        exact = r ** np.arange(n - 1, -1, -1, dtype=np.float64)
+        assert angle(X[:, l], exact) <= 1e-12
+
+
+def test_paper_h2_example_matches_printed_matrices():
+    g = read_golden_blocks(os.path.join(GOLDEN, "paper_h2_n6.txt"))
+    R, Q = hi.paper_r2_q2(6)
+    assert np.array_equal(R, g["R2"])
+    assert np.array_equal(Q, g["Q2"])
+    assert np.array_equal(R @ Q, g["H2_MINUS_GAMMA_I"])
+    assert np.array_equal(hi.paper_h2(6) - 2.0 * np.eye(6), g["H2_MINUS_GAMMA_I"])
+
+
+def test_paper_h2_solve_matches_exact_on_printed_matrix():
+    g = read_golden_blocks(os.path.join(GOLDEN, "paper_h2_n6.txt"))
+    M = g["H2_MINUS_GAMMA_I"]
+    b = np.ones(6)
+    x = solve_oracle_real(M, 0.0, b)
+    xe = exact_solve(M, 0.0, b).real
+    assert np.linalg.norm(x - xe) <= 1e-14 * np.linalg.norm(xe)
+
+
+# ------------------------------------------------------ robust scaling
+
+@pytest.mark.parametrize("n", [16, 64, 256])
+@pytest.mark.parametrize("log2_omega", [1000.0, 40.0])
+def test_good_system_h3_never_scales(n, log2_omega):
+    # Sec. 5.2: the good system never requires numerical scaling
+    H = hi.paper_h3(n)
+    x, e, C, S, rep = oracle.henry_real(H, 2.0, np.ones(n), log2_omega=log2_omega)
+    assert e == 0
+    assert np.all(np.isfinite(x))
+
+
+@pytest.mark.parametrize("n", [32, 48])
+def test_bad_system_h2_scales_and_stays_exact(n):
+    # Sec. 5.2: the bad system needs frequent scaling; with a lowered overflow
+    # threshold the scaling triggers at small n, and the scaled result must
+    # still be the exact solution's direction (all rotations are exact here)
+    H = hi.paper_h2(n)
+    x, e, C, S, rep = oracle.henry_real(H, 2.0, np.ones(n), log2_omega=30.0)
+    assert e > 0
+    y = oracle.backtransform_real(C, S, x)
+    assert np.all(np.isfinite(y))
+    xe = exact_solve(H, 2.0, np.ones(n)).real
+    assert angle(y, xe) <= 1e-13
+    # and the unscaled size really exceeds the lowered threshold
+    assert np.log2(np.abs(xe).max()) > 30.0
+
+
+def test_bad_system_h2_overflows_without_protection():
+    n = 1024
+    H = hi.paper_h2(n)
+    x, e, C, S, rep = oracle.henry_real(H, 2.0, np.ones(n), robust=False)
+    assert not np.all(np.isfinite(x))
+    x, e, C, S, rep = oracle.henry_real(H, 2.0, np.ones(n), robust=True)
+    assert np.all(np.isfinite(x)) and e > 0
+    # backward error of the scaled solve: (H - 2I) y = 2^-e b with y the
+    # backtransformed x, measured in long double
+    y = oracle.backtransform_real(C, S, x).astype(np.longdouble)
+    M = (H - 2.0 * np.eye(n)).astype(np.longdouble)
+    b = np.ones(n, dtype=np.longdouble) * np.ldexp(np.longdouble(1.0), -e)
+    r = np.abs(M @ y - b).sum()
+    assert float(r / (np.abs(M).sum(axis=0).max() * np.abs(y).sum())) <= 100 * n * EPS
+
+
+def test_graded_matrix_overflows_only_without_protection():
+    # monotone grading D = diag(10^u), u from 150 down to -150: the exact
+    # solution leaves the double range, so the unprotected solve overflows;
+    # the protected one stays finite with a small normwise residual (the
+    # algorithm is normwise backward stable; with ||G|| ~ 1e300 that is all a
+    # shift of size O(1) can promise)
+    n = 24
+    H0 = random_hessenberg(n, 11)
+    G, d = hi.graded(H0, seed=11, umax=150.0, monotone=True)
+    ev = np.linalg.eigvals(H0)
+    lam = float(ev[np.argmin(np.abs(ev.imag))].real)
+    b = hi.normal(11, 51, n)
+    with np.errstate(all="ignore"):
+        x, e, C, S, rep = oracle.henry_real(G, lam, b, robust=False)
+    assert not np.all(np.isfinite(x))
+    X, status = oracle.hsein(G, [lam], [0.0], B=b[:, None] / np.linalg.norm(b))
+    y = X[:, 0]
+    assert status[0] == 0 and np.all(np.isfinite(y)) and abs(np.linalg.norm(y) - 1) < 1e-14
+    Gl = G.astype(np.longdouble)
+    yl = y.astype(np.longdouble)
+    r = np.abs(Gl @ yl - np.longdouble(lam) * yl).sum()
+    assert float(r / (np.abs(Gl).sum(axis=0).max() * np.abs(yl).sum())) <= 100 * n * EPS
+
+
+def test_graded_eigenvector_is_d_times_eigenvector():
+    n = 16
+    H0 = random_hessenberg(n, 12)
+    G, d = hi.graded(H0, seed=12, umax=1.0)
+    ev = np.linalg.eigvals(H0)
+    lam = float(ev[np.argmin(np.abs(ev.imag))].real)
+    b = hi.normal(12, 51, n)
+    XH, sH = oracle.hsein(H0, [lam], [0.0], B=b[:, None])
+    XG, sG = oracle.hsein(G, [lam], [0.0], B=b[:, None])
+    assert sH[0] == 0 and sG[0] == 0
+    assert angle(XG[:, 0], d * XH[:, 0]) <= 1e-9
+
+
+# ------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("n", [5, 33, 64])
+def test_rotations_triangularize_shifted_matrix(n):
+    H = random_hessenberg(n, 13)
+    lam = 0.37
+    x, e, C, S, rep = oracle.henry_real(H, lam, np.ones(n))
+    assert C[0] == 1.0 and S[0] == 0.0  # padding rotation of the top-left tile
+    assert np.all(np.abs(C ** 2 + S ** 2 - 1.0) <= 4 * EPS)
+    M = H - lam * np.eye(n)
+    for k in range(n - 1, 0, -1):  # (H - lam I) G_n^T ... G_2^T = R
+        G = np.array([[C[k], -S[k]], [S[k], C[k]]])
+        M[:, [k - 1, k]] = M[:, [k - 1, k]] @ G
+    hn = np.abs(H).sum(axis=1).max()
+    assert np.abs(np.tril(M, -1)).max() <= 4 * n * EPS * hn
+    assert np.all(np.diag(M)[1:] > 0)  # phi > 0 with the chosen sign
+
+
+@pytest.mark.parametrize("n", [5, 33])
+def test_complex_rotations_triangularize(n):
+    H = random_hessenberg(n, 14)
+    lam = 0.2 + 0.9j
+    x, e, C, S, rep = oracle.henry_cplx(H, lam, np.ones(n, dtype=complex))
+    assert C[0] == 1.0 and S[0] == 0.0
+    assert np.all(np.abs(np.abs(C) ** 2 + S ** 2 - 1.0) <= 8 * EPS)
+    M = (H - lam * np.eye(n)).astype(complex)
+    for k in range(n - 1, 0, -1):
+        G = np.array([[C[k], -S[k]], [S[k], np.conj(C[k])]])
+        M[:, [k - 1, k]] = M[:, [k - 1, k]] @ G
+    hn = np.abs(H).sum(axis=1).max() + abs(lam)
+    assert np.abs(np.tril(M, -1)).max() <= 8 * n * EPS * hn
+    d = np.diag(M)[1:]
+    assert np.all(np.abs(d.imag) <= 8 * n * EPS * hn) and np.all(d.real > 0)
+
+
+def test_output_columns_have_unit_norm_and_small_residual():
+    inst = hi.small_instance(80, 8, 6, seed=3)
+    X, status = oracle.hsein(inst.H, inst.wr, inst.wi, inst.B)
+    offs = hi.column_offsets(inst.wi)
+    for l in range(inst.m):
+        if status[l] == 0:
+            nrm = np.linalg.norm(X[:, offs[l]:offs[l + 1]])
+            assert abs(nrm - 1.0) <= 4 * inst.n * EPS
+    res = residuals(inst.H, X, inst.wr, inst.wi, status)
+    ok = status == 0
+    assert ok.sum() >= inst.m - 2
+    assert np.nanmax(res[ok]) <= 100 * inst.n * EPS
+
+
+def test_config0_residuals_and_convergence():
+    inst = hi.config0()
+    X, status = oracle.hsein(inst.H, inst.wr, inst.wi, inst.B)
+    assert np.all(status == 0)
+    assert np.nanmax(residuals(inst.H, X, inst.wr, inst.wi)) <= 100 * inst.n * EPS
+
+
+def test_convergence_flag_far_and_near_shift():
+    # Varah's test (Sec. 4.2): a shift far from the spectrum gives a small
+    # solution and must be flagged (column zeroed); an eigenvalue must pass
+    inst = hi.config0()
+    H = inst.H
+    far = 1e3 * oracle.hnorm_inf(H)
+    X, status = oracle.hsein(H, [far, inst.wr[0]], [0.0, 0.0], B=inst.B[:, :2])
+    assert list(status) == [1, 0]
+    assert np.all(X[:, 0] == 0.0)
+    assert abs(np.linalg.norm(X[:, 1]) - 1.0) <= 1e-13
+
+
+def test_default_starting_vector_is_rho_e():
+    inst = hi.small_instance(40, 4, 2, seed=6)
+    X0, s0 = oracle.hsein(inst.H, inst.wr, inst.wi, None)
+    rho = EPS * oracle.hnorm_inf(inst.H)
+    B = np.zeros((inst.n, inst.ncol))
+    offs = hi.column_offsets(inst.wi)
+    for l in range(inst.m):
+        B[:, offs[l]] = rho  # complex: rho*e in the real part, 0 imaginary
+    X1, s1 = oracle.hsein(inst.H, inst.wr, inst.wi, B)
+    assert np.array_equal(X0, X1) and np.array_equal(s0, s1)
+
+
+def test_exact_eigenvalue_pivot_replacement():
+    # lambda an exact eigenvalue of an exactly representable H: the final pivot
+    # is (numerically) zero and is replaced; the result is the eigenvector
+    H = np.array([[2.0, 1.0, 0.0], [1.0, 3.0, 1.0], [0.0, 1.0, 4.0]])
+    # eigenvalue 3 has eigenvector (1, 1, -1): H (1, 1, -1) = (3, 3, -3)
+    b = np.array([[0.3], [-0.5], [0.8]])
+    X, status = oracle.hsein(H, [3.0], [0.0], B=b)
+    assert status[0] == 0
+    assert angle(X[:, 0], [1.0, 1.0, -1.0]) <= 1e-14
+    x, e, C, S, replaced = oracle.henry_real(H, 3.0, b[:, 0])
+    assert replaced
+
+
+def test_q0_apply_matches_matmul():
+    rng_Q = hi.haar_orthogonal(20, 3)
+    X = hi.normal(3, 60, 20 * 5).reshape(20, 5, order="F")
+    Z = oracle.q0_apply(rng_Q, X)
+    assert np.allclose(Z, rng_Q @ X, rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------- Hessenberg reduction
+
+@pytest.mark.parametrize("n", [3, 10, 40])
+def test_householder_reduction(n):
+    import scipy.linalg
+    A = hi.normal(21, 61, n * n).reshape(n, n, order="F")
+    H, Q = oracle.gehrd(A)
+    assert np.abs(np.tril(H, -2)).max(initial=0.0) == 0.0
+    assert np.abs(Q @ H @ Q.T - A).max() <= 10 * n * EPS * np.abs(A).max() * n
+    assert np.abs(Q.T @ Q - np.eye(n)).max() <= 10 * n * EPS
+    Hs = scipy.linalg.hessenberg(A)
+    # unique up to the signs of the reflectors: |H| agrees with LAPACK's
+    assert np.allclose(np.abs(H), np.abs(np.triu(Hs, -1)), rtol=1e-10, atol=1e-10 * np.abs(A).max())
+
+
+# ------------------------------------------------------------ generators
+
+def test_splitmix64_reference_value():
+    # seed 0 / stream 0 reduce to the plain SplitMix64 sequence from state 0,
+    # whose first output is the published 0xE220A8397B1DCDAF
+    assert int(hi.splitmix64(0, 0, 1)[0]) == 0xE220A8397B1DCDAF
+
+
+def test_generators_are_counter_based():
+    a = hi.uniform(5, 3, 100)
+    b = hi.uniform(5, 3, 40, start=60)
+    assert np.array_equal(a[60:], b)
+    z = hi.normal(9, 2, 1000)
+    assert abs(z.mean()) < 0.1 and abs(z.std() - 1) < 0.1
+
+
+def test_config0_structure():
+    inst = hi.config0(keep_a=True)
+    assert inst.n == 512 and inst.m == 64 and inst.ncol == 64
+    assert np.abs(np.tril(inst.H, -2)).max() == 0.0
+    assert np.all(inst.H[np.arange(1, 512), np.arange(511)] != 0.0)
+    assert np.abs(inst.Q0 @ inst.H @ inst.Q0.T - inst.A).max() <= 1e-10 * np.abs(inst.A).max()
+    assert np.allclose(np.linalg.norm(inst.B, axis=0), 1.0)
+    # the shifts are eigenvalues of H to working accuracy
+    ev = np.linalg.eigvals(inst.H)
+    d = np.array([np.min(np.abs(ev - w)) for w in inst.wr])
+    assert d.max() <= 1e-8 * np.abs(inst.H).max()
+
+
+def test_tiny_pivot_division_is_protected():
+    # a tiny subdiagonal and a shift that makes the last diagonal entry tiny
+    # give a pivot phi ~ 1e-300; dividing a large right-hand side by it
+    # overflows unless ProtectDivision rescales first
+    H = np.array([[1.0, 2.0, 0.5], [1e-300, 3.0, 1.0], [0.0, 1e-300, 5.0]])
+    b = np.array([1.0, 1.0, 1e20])
+    with np.errstate(all="ignore"):
+        x, e, C, S, rep = oracle.henry_real(H, 5.0, b, robust=False)
+    assert not np.all(np.isfinite(x))
+    x, e, C, S, rep = oracle.henry_real(H, 5.0, b)
+    assert e > 0 and np.all(np.isfinite(x))
+    y = oracle.backtransform_real(C, S, x)
+    xe = exact_solve(H, 5.0, b, direction=True).real
+    assert angle(y, xe) <= 1e-13
+
+
+def test_bad_system_h2_through_the_driver():
+    # the scaled solution of the bad system is astronomically large
+    # (exponent far beyond the double range), so Varah's test must pass once
+    # the exponent is counted, and the normalized vector must have a tiny
+    # residual (Sec. 4.2, Sec. 5.2)
+    n = 1024
+    H = hi.paper_h2(n)
+    X, status, exps = oracle.hsein(H, [2.0], [0.0], B=np.ones((n, 1)) / np.sqrt(n),
+                                   return_exponents=True)
+    assert status[0] == 0 and exps[0] > 900
+    assert np.all(np.isfinite(X)) and abs(np.linalg.norm(X[:, 0]) - 1.0) <= 4 * n * EPS
+    assert residual(H, 2.0, X[:, 0]) <= 100 * n * EPS
