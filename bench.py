@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Throughput benchmark: eigenvectors per second on the mixed real/complex
+workload (n = 4096; 512 real + 256 complex-conjugate shifts, i.e. 1024
+solution columns; quasi-triangular T with known eigenvalues, Haar similarity,
+Hessenberg reduction; seeded unit-norm N(0,1) starting vectors).
+
+One step = hsein_solve (all tile columns: diagonal sweeps, shared-H updates,
+normalization and Givens backtransform) + hsein_backtransform (z = Q0 x) on
+inputs resident in HBM.  H and Q0 (134 MB each) are larger than L2, so no
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own seeded instance of the same
+size (independent problems, no collective on the data path: weak scaling);
+the elapsed time is the maximum over ranks.  Rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (Henry's algorithm per shift, OpenMP
+over shifts) on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigvecs/s vs plain FP64 GPU at residual≤100nε; tensor-peak %; p50/p99 ms"
+UNIT = "eigvecs/s"
+EPS = 2.0 ** -53
+# FP64 peak: measured bf16 dense peak x the nominal FP64/BF16 ratio (1.25/2250);
+# a direct probe on this machine's GB300 measured 1.05 (DMMA), 1.01 (DFMA) and
+# 1.10 (cuBLAS DGEMM) TFLOP/s.
+NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--br", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=256, help="shifts in the oracle sample")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(", ") for r in self.file.read().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def update_flops(n, ncol, br):
+    """Algorithmic flops of all shared-H products of one solve: for every tile
+    column J >= 1 a (p0 x br) times (br x 2 ncol) product."""
+    N = (n + br - 1) // br
+    b0 = n - (N - 1) * br
+    total = 0
+    for J in range(1, N):
+        p0 = b0 + (J - 1) * br
+        total += 2 * p0 * br * 2 * ncol
+    return total, N - 1
+
+
+def source_hash(relpath):
+    with open(os.path.join(ROOT, relpath), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel_file, summary):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel; None otherwise."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != source_hash(kernel_file):
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(inst, sample_shifts):
+    """The oracle as it stands, on all host cores, on a seeded sample of the
+    workload's shifts; returns (columns/s, cores, description)."""
+    import numpy as np
+
+    import hsein_inputs as hi
+    import oracle
+    offs = hi.column_offsets(inst.wi)
+    idx = np.sort(np.argsort(hi.uniform(1234, 7, inst.m), kind="stable")[:sample_shifts])
+    wr, wi = inst.wr[idx], inst.wi[idx]
+    B = np.concatenate([inst.B[:, offs[l]:offs[l + 1]] for l in idx], axis=1)
+    oracle.hsein(inst.H[:64, :64], wr[:1] * 0, wi[:1] * 0, None)  # load and warm the library
+    t0 = time.perf_counter()
+    X, st = oracle.hsein(inst.H, wr, wi, B)
+    Z = oracle.q0_apply(inst.Q0, X)
+    dt = time.perf_counter() - t0
+    cols = X.shape[1]
+    cores = os.cpu_count()
+    desc = ("%d of %d shifts (%d columns) of the same instance: Henry solve + normalization + "
+            "backtransform + z = Q0 x, OpenMP over shifts, %.2f s wall" % (len(idx), inst.m, cols, dt))
+    return cols / dt, cores, desc
+
+
+def run_reference(args):
+    """The oracle on the host cores, on the same workload, each step a bounded
+    sample of its shifts."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import hsein_inputs as hi
+    import oracle
+    inst = hi.config1(seed=1)
+    offs = hi.column_offsets(inst.wi)
+    per_step = 96
+    order = np.argsort(hi.uniform(4321, 7, inst.m), kind="stable")
+
+    def step(s):
+        idx = order[(s * per_step) % inst.m:(s * per_step) % inst.m + per_step]
+        wr, wi = inst.wr[idx], inst.wi[idx]
+        B = np.concatenate([inst.B[:, offs[l]:offs[l + 1]] for l in idx], axis=1)
+        X, st = oracle.hsein(inst.H, wr, wi, B)
+        oracle.q0_apply(inst.Q0, X)
+        return X.shape[1]
+
+    for s in range(args.warmup):
+        step(s)
+    t0 = time.perf_counter()
+    cols = 0
+    for s in range(args.steps):
+        cols += step(args.warmup + s)
+    dt = time.perf_counter() - t0
+    value = cols / dt
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(inst, args.br),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d shifts per step of the same instance (Henry solve + "
+                                   "normalization + backtransform + z = Q0 x)" % per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(inst, br):
+    return {
+        "workload": "mixed real/complex shifts: n=4096, 512 real + 256 complex shifts "
+                    "(1024 columns), FP64 products, tile height %d" % br,
+        "n": inst.n, "m_real": inst.m_real, "m_cplx": inst.m_cplx, "columns": inst.ncol,
+        "br": br, "precision": "fp64",
+        "l2": "no flush: H and Q0 (134 MB each) are larger than L2",
+    }
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import hsein_inputs as hi
+    import paper_2101_05063_gb300 as hs
+
+    rank, world, local = dist_setup()
+    dev = torch.device("cuda", local)
+    inst = hi.config1(seed=1 + rank)
+    n, ncol, m = inst.n, inst.ncol, inst.m
+    f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device=dev)
+    dH, dwr, dwi, dB, dQ = f(inst.H), f(inst.wr), f(inst.wi), f(inst.B), f(inst.Q0)
+    solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=args.br, device=dev)
+    X = torch.empty((ncol, n), dtype=torch.float64, device=dev).t()
+    Z = torch.empty((ncol, n), dtype=torch.float64, device=dev).t()
+    status = torch.empty(m, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        solver.solve(dH, dwr, dwi, dB, X=X, status=status, check=False)
+        solver.backtransform(dQ, X, Z=Z)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    dstat = solver.device_status()
+    if dstat < 0:
+        raise RuntimeError("device status %d" % dstat)
+    # accuracy of this run: normwise residual of every converged column
+    sh = status.cpu().numpy()
+    HX = (dH @ X).cpu().numpy()
+    Xh = X.cpu().numpy()
+    offs = hi.column_offsets(inst.wi)
+    hn1 = np.abs(inst.H).sum(axis=0).max()
+    worst = 0.0
+    for l in range(m):
+        if sh[l] != 0:
+            continue
+        c0, c1 = offs[l], offs[l + 1]
+        if c1 - c0 == 2:
+            lam = complex(inst.wr[l], inst.wi[l])
+            x, hx = Xh[:, c0] + 1j * Xh[:, c0 + 1], HX[:, c0] + 1j * HX[:, c0 + 1]
+        else:
+            lam, x, hx = inst.wr[l], Xh[:, c0], HX[:, c0]
+        worst = max(worst, np.abs(hx - lam * x).sum() / (hn1 * np.abs(x).sum()))
+
+    # ---------------- timed region: device-resident inputs ------------------
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    hs.hsein_plan_set_profiling(solver.plan, True)
+    hs.hsein_plan_profile(solver.plan, reset=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    prof = hs.hsein_plan_profile(solver.plan, reset=True)
+    hs.hsein_plan_set_profiling(solver.plan, False)
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(ms, world)
+    value = world * ncol * args.steps / (ms * 1e-3)
+
+    # ---------------- end to end through the API with host buffers ---------
+    pin = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64).pin_memory()
+    hH, hwr, hwi, hB, hQ = pin(inst.H), pin(inst.wr), pin(inst.wi), pin(inst.B), pin(inst.Q0)
+    hZ = torch.empty((ncol, n), dtype=torch.float64).pin_memory().t()
+    hS = torch.empty(m, dtype=torch.int32).pin_memory()
+    h2d = 8 * (2 * n * n + n * ncol + 2 * m)
+    d2h = 8 * n * ncol + 4 * m
+
+    def e2e_step():
+        dH.copy_(hH, non_blocking=True)
+        dwr.copy_(hwr, non_blocking=True)
+        dwi.copy_(hwi, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        dQ.copy_(hQ, non_blocking=True)
+        step()
+        hZ.copy_(Z, non_blocking=True)
+        hS.copy_(status, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = world * ncol * args.steps / (ms_e2e * 1e-3)
+
+    if rank != 0:
+        return
+    pk, pk_kind = peaks()
+    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16  # TFLOP/s
+    uf, ulaunch = update_flops(n, ncol, args.br)
+    q0f = 2.0 * n * n * ncol
+    phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+              for k, v in prof.items()}
+    dominant = max(prof, key=lambda k: prof[k][0])
+    if dominant == "q0_backtransform":
+        flops_launch, t_launch = q0f, prof[dominant][0] / max(1, prof[dominant][1])
+        kfile, summary = "paper_2101_05063_gb300/csrc/k_q0.cu", "k_q0_config1.txt"
+        kname = "k_q0"
+    else:
+        flops_launch = uf / ulaunch
+        t_launch = prof["shared_h_update"][0] / max(1, prof["shared_h_update"][1])
+        kfile, summary = "paper_2101_05063_gb300/csrc/k_update.cu", "k_update_config1.txt"
+        kname = "k_update"
+        dominant = "shared_h_update"
+    achieved = flops_launch / (t_launch * 1e-3) / 1e12
+    # prepare is four kernels (setup, row sums, tile norms, init); the other
+    # phases are one kernel per recorded launch
+    launches = 4 * prof["prepare"][1] + sum(v[1] for k, v in prof.items() if k != "prepare")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(inst, args.br),
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "traffic": profiled_traffic(kfile, summary),
+                     "peak_source": "FP64: %s bf16 %.1f TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
+                                    % (pk_kind, pk["bf16_tflops"]),
+                     "algorithmic_flops_per_launch": flops_launch},
+        "phases": phases,
+        "residual_max_over_n_eps": worst / (n * EPS),
+        "not_converged": int((sh != 0).sum()),
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        v, cores, desc = cpu_baseline(inst, args.cpu_sample)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * hsein.h -- C ABI of a GB300 (sm_103a) library that computes eigenvectors of
+ * a real upper Hessenberg matrix H by one step of inverse iteration for many
+ * shifts at once:  (H - lambda_l I) x_l = alpha_l b_l,  l = 1..m,
+ * following Schwarz, "Robust level-3 BLAS Inverse Iteration from the
+ * Hessenberg Matrix" (arXiv 2101.05063).
+ *
+ * The solve is Henry's RQ approach (Sec. 2.2, Alg. "henry") rearranged by
+ * tiles (Sec. 3): every shift gets its own Givens sweep over the diagonal
+ * tiles (Alg. "tiled-reduction1", "solve"), while the updates of all rows
+ * above a diagonal tile read one block of H shared by every shift and run as
+ * one dense matrix-matrix product over the whole block of shifts (eq.
+ * "update", Alg. "tile-update"; the off-diagonal reduction of Alg.
+ * "tiled-reduction2" joins the same product).  Every solution column carries
+ * an exact power-of-two scale factor so that nothing overflows (Sec. 4.1,
+ * eq. "robust-update"); the result is normalized with a scaled 2-norm and
+ * backtransformed (Alg. "consistency-scaling"), and Varah's test flags
+ * columns that did not converge (Sec. 4.2).  Complex shifts use the rotation
+ * of eq. "cgivens" (Sec. 4.3).
+ *
+ * Conventions (all calls):
+ *  - Matrices are double precision, column-major, with a leading dimension.
+ *  - A real shift owns one column of B, X and Z; a complex shift (wi != 0;
+ *    pass one member of each conjugate pair) owns two adjacent columns
+ *    [real part, imaginary part].  Columns follow the input order of shifts.
+ *  - Device pointers: memory of the current CUDA device.  The caller owns
+ *    every buffer, including the workspace; the plan owns host metadata only.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered and asynchronous: the returned status reports argument
+ *    errors found at enqueue time and CUDA launch errors.  Errors found on the
+ *    device (non-finite or reduced H, wrong shift count) are recorded in the
+ *    workspace; read them with hsein_plan_sync_status.  No exception crosses
+ *    this interface.  A plan is not thread-safe; distinct plans are.
+ */
+#ifndef HSEIN_H
+#define HSEIN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hsein_plan_s *hsein_plan_t;
+
+typedef enum {
+    HSEIN_OK = 0,
+    HSEIN_EARG = -1,          /* invalid argument (value or pointer)                    */
+    HSEIN_ENOMEM = -2,        /* host allocation failed or workspace too small           */
+    HSEIN_ENOTUNREDUCED = -3, /* device: some subdiagonal entry h(k,k-1) is zero          */
+    HSEIN_ENONFINITE = -4,    /* device: H or a shift contains Inf or NaN                 */
+    HSEIN_ECUDA = -5,         /* a CUDA call or kernel launch failed                      */
+    HSEIN_ESHIFTS = -7,       /* device: the number of wi != 0 differs from m_cplx        */
+    HSEIN_WNOTCONVERGED = 1   /* device: some column failed Varah's test (zeroed)         */
+} hsein_status;
+
+/* Per-shift status written by hsein_solve to dStatus[l]. */
+enum {
+    HSEIN_COL_OK = 0,            /* converged, column holds a unit-norm vector        */
+    HSEIN_COL_NOT_CONVERGED = 1, /* failed Varah's test (Sec. 4.2), column set to 0   */
+    HSEIN_COL_INVALID = 3        /* the solve did not run (device error, see above)   */
+};
+
+typedef struct {
+    int br;         /* tile height b_r (Sec. 3.2), 8..128; 0 = default (64)                 */
+    int precision;  /* 0 = FP64 products (the only mode of this version)                     */
+    int robust;     /* 1 = overflow protection (default); 0 = off, for tests that show       */
+                    /*     what the protection prevents                                      */
+    int omega_log2; /* stored solution entries stay below 2^omega_log2; 0 = default (1000).  */
+                    /* Lower values (>= 16) make the scaling of Sec. 4.1 trigger on small     */
+                    /* problems, for testing                                                 */
+    int reserved[4];
+} hsein_options;
+
+/* Fill *opt with the defaults.  Returns HSEIN_EARG for opt == NULL. */
+hsein_status hsein_default_options(hsein_options *opt);
+
+/*
+ * Create a plan for n x n matrices and m_real real plus m_cplx complex shifts
+ * (ncol = m_real + 2 m_cplx solution columns).  opt may be NULL (defaults).
+ * *workspace_bytes receives the device workspace size hsein_solve and
+ * hsein_backtransform need.  n >= 1, m_real >= 0, m_cplx >= 0,
+ * m_real + m_cplx >= 1.  On error *plan is set to NULL.
+ */
+hsein_status hsein_plan(hsein_plan_t *plan, int n, int m_real, int m_cplx,
+                        const hsein_options *opt, size_t *workspace_bytes);
+
+/*
+ * Solve (H - lambda_l I) x_l = alpha_l b_l for every shift and store unit
+ * 2-norm eigenvector approximations of H in dX (Alg. "hsrq3" followed by the
+ * convergence test of Sec. 4.2).
+ *   dH      n x n upper Hessenberg, leading dimension ldh >= n; entries below
+ *           the first subdiagonal are not read.  Every h(k,k-1) must be nonzero
+ *           (H unreduced, Sec. 1).
+ *   dWr,dWi m = m_real + m_cplx shifts lambda_l = wr_l + i wi_l; exactly m_cplx
+ *           of them have wi != 0 (one member per conjugate pair, Sec. 4.3).
+ *   dB      n x ncol starting vectors (ldb >= n) or NULL for rho*e with
+ *           rho = eps ||H||_inf (Sec. 4.2; for a complex shift rho*e + 0i).
+ *   dX      n x ncol output (ldx >= n); may not alias dB or dH.
+ *   dStatus m per-shift codes (HSEIN_COL_*), in input order.
+ *   dWork   device workspace of at least the size hsein_plan reported,
+ *           256-byte aligned; contents on entry are irrelevant.
+ * The eigenvectors are normalized to ||x||_2 = 1; their sign (real) or phase
+ * (complex) is not normalized.  Work is enqueued on `stream`.
+ */
+hsein_status hsein_solve(hsein_plan_t plan, const double *dH, int ldh,
+                         const double *dWr, const double *dWi,
+                         const double *dB, int ldb, double *dX, int ldx,
+                         int *dStatus, void *dWork, size_t work_bytes, void *stream);
+
+/*
+ * z_l = Q0 x_l for every column (Sec. 1: H = Q0^T A Q0 maps eigenvectors of H
+ * to eigenvectors of A).  dQ0 n x n (ldq >= n), dX n x ncol (ldx >= n), dZ
+ * n x ncol output (ldz >= n, may not alias dX).  dWork as for hsein_solve
+ * (the same buffer may be reused after the solve).  Stream-ordered.
+ */
+hsein_status hsein_backtransform(hsein_plan_t plan, const double *dQ0, int ldq,
+                                 const double *dX, int ldx, double *dZ, int ldz,
+                                 void *dWork, size_t work_bytes, void *stream);
+
+/*
+ * Wait for `stream`, then return the device-side status of the last
+ * hsein_solve that used dWork: HSEIN_OK, HSEIN_WNOTCONVERGED, or one of the
+ * device error codes.  Returns HSEIN_ECUDA if the stream reports an error.
+ */
+hsein_status hsein_plan_sync_status(hsein_plan_t plan, const void *dWork, void *stream);
+
+/*
+ * Per-phase device timing for measurement.  While enabled, every kernel
+ * launch of hsein_solve / hsein_backtransform on this plan is bracketed by
+ * CUDA events on the caller's stream (no synchronization is added).
+ * hsein_plan_profile waits for the last recorded event and returns, per phase,
+ * the summed milliseconds and the number of launches since the last reset:
+ *   phase 0 prepare (norms, prescale, initial state)
+ *   phase 1 diagonal-tile sweep and solve (one launch per tile column)
+ *   phase 2 shared-H update product (one launch per tile column but the last)
+ *   phase 3 normalization and Givens backtransform
+ *   phase 4 z = Q0 x
+ * ms and launches point to arrays of nphases (<= HSEIN_NUM_PHASES) entries;
+ * reset != 0 clears the record afterwards.
+ */
+#define HSEIN_NUM_PHASES 5
+hsein_status hsein_plan_set_profiling(hsein_plan_t plan, int enable);
+hsein_status hsein_plan_profile(hsein_plan_t plan, double *ms, int *launches, int nphases,
+                                int reset);
+
+/* Query the plan's sizes; any output pointer may be NULL. */
+hsein_status hsein_plan_info(hsein_plan_t plan, int *n, int *m_real, int *m_cplx,
+                             int *ncol, int *br, size_t *workspace_bytes);
+
+/* Release the plan (NULL is accepted). */
+hsein_status hsein_plan_destroy(hsein_plan_t plan);
+
+/* Static, human-readable text for a status code. */
+const char *hsein_status_string(hsein_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSEIN_H */

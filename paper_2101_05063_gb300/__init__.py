@@ -1,0 +1,249 @@
+"""GB300-native multi-shift inverse iteration from the Hessenberg matrix.
+
+Python binding of libhsein (C ABI in include/hsein.h).  The functions named
+like the C entry points (hsein_plan, hsein_solve, hsein_backtransform, ...)
+only marshal arguments; every step of the computation runs in the CUDA
+kernels of the library.  PyTorch provides device memory and streams.  There
+is no CPU fallback: if the library cannot be loaded, every call raises.
+
+    import torch, paper_2101_05063_gb300 as hs
+    solver = hs.Solver(n, m_real, m_cplx)             # plan + workspace
+    X, status = solver.solve(H, wr, wi, B)            # unit eigenvectors of H
+    Z = solver.backtransform(Q0, X)                   # eigenvectors of A
+
+Column layout (as in the C ABI): a real shift owns one column, a complex
+shift two adjacent columns [re, im], in the input order of the shifts.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "HseinError", "HseinOptions", "load", "hsein_default_options", "hsein_plan", "hsein_solve",
+    "hsein_backtransform", "hsein_plan_sync_status", "hsein_plan_info", "hsein_plan_destroy",
+    "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
+    "STATUS", "PHASES",
+]
+
+STATUS = {0: "HSEIN_OK", -1: "HSEIN_EARG", -2: "HSEIN_ENOMEM", -3: "HSEIN_ENOTUNREDUCED",
+          -4: "HSEIN_ENONFINITE", -5: "HSEIN_ECUDA", -7: "HSEIN_ESHIFTS", 1: "HSEIN_WNOTCONVERGED"}
+
+
+class HseinError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = int(code)
+        msg = "%s (%d)" % (STATUS.get(self.code, "unknown"), self.code)
+        if what:
+            msg = what + ": " + msg
+        super().__init__(msg)
+
+
+class HseinOptions(ctypes.Structure):
+    _fields_ = [("br", ctypes.c_int), ("precision", ctypes.c_int), ("robust", ctypes.c_int),
+                ("omega_log2", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+_lib = None
+
+
+def load(build_if_missing=True):
+    """Load libhsein.so (building it with nvcc first if it is missing or
+    stale).  Raises if it cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise HseinError(-5, "libhsein.so is missing (%s); run build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, sz, ip, dp = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p
+    lib.hsein_default_options.restype = ctypes.c_int
+    lib.hsein_default_options.argtypes = [ctypes.POINTER(HseinOptions)]
+    lib.hsein_plan.restype = ctypes.c_int
+    lib.hsein_plan.argtypes = [ctypes.POINTER(vp), ip, ip, ip, ctypes.POINTER(HseinOptions),
+                               ctypes.POINTER(sz)]
+    lib.hsein_solve.restype = ctypes.c_int
+    lib.hsein_solve.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, vp, sz, vp]
+    lib.hsein_backtransform.restype = ctypes.c_int
+    lib.hsein_backtransform.argtypes = [vp, dp, ip, dp, ip, dp, ip, vp, sz, vp]
+    lib.hsein_plan_sync_status.restype = ctypes.c_int
+    lib.hsein_plan_sync_status.argtypes = [vp, vp, vp]
+    lib.hsein_plan_info.restype = ctypes.c_int
+    lib.hsein_plan_info.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5 + [ctypes.POINTER(sz)]
+    lib.hsein_plan_destroy.restype = ctypes.c_int
+    lib.hsein_plan_destroy.argtypes = [vp]
+    lib.hsein_status_string.restype = ctypes.c_char_p
+    lib.hsein_status_string.argtypes = [ctypes.c_int]
+    lib.hsein_plan_set_profiling.restype = ctypes.c_int
+    lib.hsein_plan_set_profiling.argtypes = [vp, ip]
+    lib.hsein_plan_profile.restype = ctypes.c_int
+    lib.hsein_plan_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int), ip, ip]
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------- C-ABI mirrors
+
+def hsein_default_options():
+    o = HseinOptions()
+    _check(load().hsein_default_options(ctypes.byref(o)), "hsein_default_options")
+    return o
+
+
+def hsein_plan(n, m_real, m_cplx, opt=None):
+    """Returns (plan handle, workspace bytes)."""
+    p = ctypes.c_void_p()
+    w = ctypes.c_size_t()
+    rc = load().hsein_plan(ctypes.byref(p), int(n), int(m_real), int(m_cplx),
+                           ctypes.byref(opt) if opt is not None else None, ctypes.byref(w))
+    _check(rc, "hsein_plan")
+    return p, w.value
+
+
+def hsein_solve(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, dWork, work_bytes, stream):
+    """Device pointers are integers (e.g. tensor.data_ptr()); dB may be 0."""
+    return load().hsein_solve(plan, dH, ldh, dWr, dWi, dB or None, ldb, dX, ldx, dStatus, dWork,
+                              work_bytes, stream or None)
+
+
+def hsein_backtransform(plan, dQ0, ldq, dX, ldx, dZ, ldz, dWork, work_bytes, stream):
+    return load().hsein_backtransform(plan, dQ0, ldq, dX, ldx, dZ, ldz, dWork, work_bytes,
+                                      stream or None)
+
+
+def hsein_plan_sync_status(plan, dWork, stream):
+    return load().hsein_plan_sync_status(plan, dWork, stream or None)
+
+
+def hsein_plan_info(plan):
+    vals = [ctypes.c_int() for _ in range(5)]
+    w = ctypes.c_size_t()
+    _check(load().hsein_plan_info(plan, *[ctypes.byref(v) for v in vals], ctypes.byref(w)),
+           "hsein_plan_info")
+    n, mr, mc, ncol, br = (v.value for v in vals)
+    return dict(n=n, m_real=mr, m_cplx=mc, ncol=ncol, br=br, workspace_bytes=w.value)
+
+
+def hsein_plan_destroy(plan):
+    return load().hsein_plan_destroy(plan)
+
+
+def hsein_status_string(code):
+    return load().hsein_status_string(int(code)).decode()
+
+
+PHASES = ["prepare", "diag_sweep", "shared_h_update", "finalize", "q0_backtransform"]
+
+
+def hsein_plan_set_profiling(plan, enable):
+    return _check(load().hsein_plan_set_profiling(plan, int(bool(enable))),
+                  "hsein_plan_set_profiling")
+
+
+def hsein_plan_profile(plan, reset=True):
+    """{phase: (milliseconds, launches)} since the last reset."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    _check(load().hsein_plan_profile(plan, ms, cnt, n, int(bool(reset))), "hsein_plan_profile")
+    return {PHASES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise HseinError(rc, what)
+    return rc
+
+
+# ------------------------------------------------------ torch convenience
+
+def _colmajor(t, torch):
+    """A column-major (Fortran-order) float64 view or copy of a 2-D tensor."""
+    if t.dim() == 1:
+        t = t.reshape(-1, 1)
+    if t.dtype != torch.float64:
+        raise TypeError("expected float64, got %s" % t.dtype)
+    if t.stride(0) == 1 and (t.shape[1] <= 1 or t.stride(1) >= max(1, t.shape[0])):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t):
+    """Leading dimension of a column-major tensor (for one column any value
+    >= the row count is valid, whatever stride torch reports)."""
+    return t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])
+
+
+class Solver:
+    """A plan plus its device workspace for fixed (n, m_real, m_cplx).
+
+    solve() and backtransform() take CUDA float64 tensors (any layout; they are
+    used in place when already column-major) and run on the current stream.
+    """
+
+    def __init__(self, n, m_real, m_cplx, br=64, robust=True, omega_log2=1000, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            opt = hsein_default_options()
+            opt.br = int(br)
+            opt.robust = int(bool(robust))
+            opt.omega_log2 = int(omega_log2)
+            self.plan, self.work_bytes = hsein_plan(n, m_real, m_cplx, opt)
+        self.n, self.m_real, self.m_cplx = int(n), int(m_real), int(m_cplx)
+        self.m = self.m_real + self.m_cplx
+        self.ncol = self.m_real + 2 * self.m_cplx
+        self.work = torch.empty(self.work_bytes, dtype=torch.uint8, device=self.device)
+
+    def __del__(self):
+        plan = getattr(self, "plan", None)
+        if plan is not None and _lib is not None:
+            _lib.hsein_plan_destroy(plan)
+            self.plan = None
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def solve(self, H, wr, wi, B=None, X=None, status=None, check=True):
+        """Returns (X, status): unit-norm eigenvector approximations of H
+        (n x ncol, column-major) and per-shift codes (0 ok, 1 not converged)."""
+        torch = self.torch
+        H = _colmajor(H, torch)
+        wr = wr.to(torch.float64).contiguous()
+        wi = wi.to(torch.float64).contiguous()
+        if B is not None:
+            B = _colmajor(B, torch)
+        if X is None:
+            X = torch.empty((self.ncol, self.n), dtype=torch.float64, device=self.device).t()
+        if status is None:
+            status = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        rc = hsein_solve(self.plan, H.data_ptr(), _ld(H), wr.data_ptr(), wi.data_ptr(),
+                         B.data_ptr() if B is not None else 0, _ld(B) if B is not None else self.n,
+                         X.data_ptr(), _ld(X), status.data_ptr(), self.work.data_ptr(),
+                         self.work_bytes, self._stream())
+        _check(rc, "hsein_solve")
+        if check:
+            rc = hsein_plan_sync_status(self.plan, self.work.data_ptr(), self._stream())
+            _check(rc, "hsein_solve (device)")
+        return X, status
+
+    def device_status(self):
+        return hsein_plan_sync_status(self.plan, self.work.data_ptr(), self._stream())
+
+    def backtransform(self, Q0, X, Z=None):
+        """Z = Q0 X (eigenvectors of A = Q0 H Q0^T)."""
+        torch = self.torch
+        Q0 = _colmajor(Q0, torch)
+        X = _colmajor(X, torch)
+        if Z is None:
+            Z = torch.empty((self.ncol, self.n), dtype=torch.float64, device=self.device).t()
+        rc = hsein_backtransform(self.plan, Q0.data_ptr(), _ld(Q0), X.data_ptr(), _ld(X),
+                                 Z.data_ptr(), _ld(Z), self.work.data_ptr(), self.work_bytes,
+                                 self._stream())
+        _check(rc, "hsein_backtransform")
+        return Z

@@ -1,0 +1,294 @@
+// Host side of the C ABI declared in include/hsein.h: argument checks, the
+// workspace layout and the launch sequence of one solve.
+//
+// Launch sequence of hsein_solve (all on the caller's stream):
+//   prepare (setup, row sums, tile norms, init)            -- step a0
+//   for J = N-1 .. 1:  k_diag(J)  then  k_update(J)          -- steps a1..a4
+//   k_diag(0)                                               -- top-left tile
+//   k_finalize                                              -- step a5
+// The tile columns are walked once from right to left: the cross-over
+// columns needed by the update of tile column J are produced by the same
+// product that performs that update, so only one n x ncol buffer of
+// cross-over columns is live (the paper stores N of them per shift,
+// Sec. 4.4, and must group shifts because of it).
+#include "../../include/hsein.h"
+#include "common.cuh"
+
+#include <cstdint>
+#include <cstdlib>
+#include <new>
+#include <vector>
+
+namespace hsein {
+cudaError_t diag_configure(int br);
+cudaError_t update_configure(int br);
+}  // namespace hsein
+
+using hsein::Layout;
+
+struct hsein_plan_s {
+    Layout L;
+    hsein_options opt;
+    int device;
+    // measurement: one (phase, start, end) record per launch while enabled
+    int profiling = 0;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<int> rec_phase;
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void make_layout(Layout* L, int n, int mr, int mc, int br) {
+    L->n = n;
+    L->mr = mr;
+    L->mc = mc;
+    L->m = mr + mc;
+    L->ncol = mr + 2 * mc;
+    L->ncolp = (L->ncol + 31) / 32 * 32;
+    L->br = br;
+    L->N = (n + br - 1) / br;
+    L->b0 = n - (L->N - 1) * br;
+    L->ldw = (n + 7) / 8 * 8;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    const size_t m = (size_t)L->m, N = (size_t)L->N, nn = (size_t)n;
+    L->off_state = take(sizeof(hsein::DevState));
+    L->off_qsrc = take(sizeof(int) * m);
+    L->off_qcol = take(sizeof(int) * m);
+    L->off_lam = take(sizeof(double) * 2 * m);
+    L->off_bnorm = take(sizeof(double) * m);
+    L->off_eB = take(sizeof(int) * m);
+    L->off_etile = take(sizeof(int) * N * m);
+    L->off_bmax = take(sizeof(unsigned long long) * m);
+    L->off_rmax = take(sizeof(unsigned long long) * m);
+    L->off_epi = take(sizeof(hsein::Epi) * m);
+    L->off_anorm = take(sizeof(unsigned long long) * N);
+    L->off_rowpart = take(sizeof(double) * nn * (N + 1));
+    L->off_X = take(sizeof(double) * (size_t)L->ldw * L->ncolp);
+    L->off_R = take(sizeof(double) * (size_t)L->ldw * L->ncolp);
+    L->off_Cr = take(sizeof(double) * nn * m);
+    L->off_Ci = take(sizeof(double) * nn * (size_t)(mc > 0 ? mc : 1));
+    L->off_S = take(sizeof(double) * nn * m);
+    L->off_ZW = take(sizeof(double) * (size_t)br * 2 * L->ncolp);
+    L->total = o;
+}
+
+bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
+
+cudaEvent_t next_event(hsein_plan_s* p) {
+    if (p->used == p->pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p->pool.push_back(e);
+    }
+    return p->pool[p->used++];
+}
+
+// brackets one launch with events when profiling is on
+struct PhaseScope {
+    hsein_plan_s* p;
+    cudaStream_t s;
+    PhaseScope(hsein_plan_s* plan, int phase, cudaStream_t stream) : p(plan), s(stream) {
+        if (!p->profiling) return;
+        cudaEvent_t e = next_event(p);
+        if (e) {
+            cudaEventRecord(e, s);
+            p->rec_phase.push_back(phase);
+        }
+    }
+    ~PhaseScope() {
+        if (!p->profiling) return;
+        cudaEvent_t e = next_event(p);
+        if (e) cudaEventRecord(e, s);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+hsein_status hsein_default_options(hsein_options* opt) {
+    if (!opt) return HSEIN_EARG;
+    *opt = hsein_options{};
+    opt->br = 64;
+    opt->precision = 0;
+    opt->robust = 1;
+    opt->omega_log2 = 1000;
+    return HSEIN_OK;
+}
+
+hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
+                        const hsein_options* opt, size_t* workspace_bytes) {
+    if (!plan) return HSEIN_EARG;
+    *plan = nullptr;
+    if (n < 1 || m_real < 0 || m_cplx < 0 || m_real + m_cplx < 1) return HSEIN_EARG;
+    if ((long long)m_real + 2LL * m_cplx > (1LL << 30)) return HSEIN_EARG;
+    hsein_options o;
+    hsein_default_options(&o);
+    if (opt) {
+        if (opt->br != 0) o.br = opt->br;
+        o.precision = opt->precision;
+        o.robust = opt->robust;
+        if (opt->omega_log2 != 0) o.omega_log2 = opt->omega_log2;
+    }
+    if (o.br < 8 || o.br > hsein::kMaxBr) return HSEIN_EARG;
+    if (o.precision != 0) return HSEIN_EARG;
+    if (o.robust != 0 && o.robust != 1) return HSEIN_EARG;
+    if (o.omega_log2 < 16 || o.omega_log2 > 1000) return HSEIN_EARG;
+    hsein_plan_s* p = new (std::nothrow) hsein_plan_s;
+    if (!p) return HSEIN_ENOMEM;
+    make_layout(&p->L, n, m_real, m_cplx, o.br);
+    p->opt = o;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        hsein::diag_configure(o.br) != cudaSuccess || hsein::update_configure(o.br) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return HSEIN_ECUDA;
+    }
+    if (workspace_bytes) *workspace_bytes = p->L.total;
+    *plan = p;
+    return HSEIN_OK;
+}
+
+hsein_status hsein_plan_info(hsein_plan_t plan, int* n, int* m_real, int* m_cplx, int* ncol,
+                             int* br, size_t* workspace_bytes) {
+    if (!plan) return HSEIN_EARG;
+    if (n) *n = plan->L.n;
+    if (m_real) *m_real = plan->L.mr;
+    if (m_cplx) *m_cplx = plan->L.mc;
+    if (ncol) *ncol = plan->L.ncol;
+    if (br) *br = plan->L.br;
+    if (workspace_bytes) *workspace_bytes = plan->L.total;
+    return HSEIN_OK;
+}
+
+hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const double* dWr,
+                         const double* dWi, const double* dB, int ldb, double* dX, int ldx,
+                         int* dStatus, void* dWork, size_t work_bytes, void* stream) {
+    if (!plan) return HSEIN_EARG;
+    const Layout& L = plan->L;
+    if (!dH || ldh < L.n || !dWr || !dWi || !dX || ldx < L.n || !dStatus) return HSEIN_EARG;
+    if (dB && ldb < L.n) return HSEIN_EARG;
+    if (!dWork || !aligned256(dWork)) return HSEIN_EARG;
+    if (work_bytes < L.total) return HSEIN_ENOMEM;
+    if ((const void*)dX == (const void*)dH || (dB && (const void*)dX == (const void*)dB))
+        return HSEIN_EARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int robust = plan->opt.robust, om = plan->opt.omega_log2;
+    {
+        PhaseScope ps(plan, 0, s);
+        hsein::launch_prepare(L, dWork, dH, ldh, dWr, dWi, dB, ldb, om, s);
+    }
+    for (int J = L.N - 1; J >= 1; --J) {
+        {
+            PhaseScope ps(plan, 1, s);
+            hsein::launch_diag(L, dWork, dH, ldh, J, robust, om, s);
+        }
+        PhaseScope ps(plan, 2, s);
+        hsein::launch_update(L, dWork, dH, ldh, J, s);
+    }
+    {
+        PhaseScope ps(plan, 1, s);
+        hsein::launch_diag(L, dWork, dH, ldh, 0, robust, om, s);
+    }
+    {
+        PhaseScope ps(plan, 3, s);
+        hsein::launch_finalize(L, dWork, dX, ldx, dStatus, s);
+    }
+    if (cudaGetLastError() != cudaSuccess) return HSEIN_ECUDA;
+    return HSEIN_OK;
+}
+
+hsein_status hsein_backtransform(hsein_plan_t plan, const double* dQ0, int ldq, const double* dX,
+                                 int ldx, double* dZ, int ldz, void* dWork, size_t work_bytes,
+                                 void* stream) {
+    if (!plan) return HSEIN_EARG;
+    const Layout& L = plan->L;
+    if (!dQ0 || ldq < L.n || !dX || ldx < L.n || !dZ || ldz < L.n) return HSEIN_EARG;
+    if ((const void*)dZ == (const void*)dX || (const void*)dZ == (const void*)dQ0) return HSEIN_EARG;
+    (void)dWork;
+    (void)work_bytes;
+    {
+        PhaseScope ps(plan, 4, static_cast<cudaStream_t>(stream));
+        hsein::launch_q0(L, dQ0, ldq, dX, ldx, dZ, ldz, static_cast<cudaStream_t>(stream));
+    }
+    if (cudaGetLastError() != cudaSuccess) return HSEIN_ECUDA;
+    return HSEIN_OK;
+}
+
+hsein_status hsein_plan_sync_status(hsein_plan_t plan, const void* dWork, void* stream) {
+    if (!plan || !dWork) return HSEIN_EARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st = 0;
+    const char* base = static_cast<const char*>(dWork) + plan->L.off_state;
+    if (cudaMemcpyAsync(&st, base + offsetof(hsein::DevState, status), sizeof(int),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return HSEIN_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HSEIN_ECUDA;
+    return static_cast<hsein_status>(st);
+}
+
+hsein_status hsein_plan_set_profiling(hsein_plan_t plan, int enable) {
+    if (!plan) return HSEIN_EARG;
+    plan->profiling = enable ? 1 : 0;
+    return HSEIN_OK;
+}
+
+hsein_status hsein_plan_profile(hsein_plan_t plan, double* ms, int* launches, int nphases,
+                                int reset) {
+    if (!plan || nphases < 0 || nphases > HSEIN_NUM_PHASES) return HSEIN_EARG;
+    for (int i = 0; i < nphases; ++i) {
+        if (ms) ms[i] = 0.0;
+        if (launches) launches[i] = 0;
+    }
+    const size_t nrec = plan->rec_phase.size();
+    if (nrec > 0) {
+        if (cudaEventSynchronize(plan->pool[2 * nrec - 1]) != cudaSuccess) return HSEIN_ECUDA;
+        for (size_t r = 0; r < nrec; ++r) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, plan->pool[2 * r], plan->pool[2 * r + 1]) != cudaSuccess)
+                return HSEIN_ECUDA;
+            int ph = plan->rec_phase[r];
+            if (ph < nphases) {
+                if (ms) ms[ph] += t;
+                if (launches) launches[ph] += 1;
+            }
+        }
+    }
+    if (reset) {
+        plan->used = 0;
+        plan->rec_phase.clear();
+    }
+    return HSEIN_OK;
+}
+
+hsein_status hsein_plan_destroy(hsein_plan_t plan) {
+    if (plan) {
+        for (cudaEvent_t e : plan->pool) cudaEventDestroy(e);
+    }
+    delete plan;
+    return HSEIN_OK;
+}
+
+const char* hsein_status_string(hsein_status status) {
+    switch (status) {
+        case HSEIN_OK: return "ok";
+        case HSEIN_EARG: return "invalid argument";
+        case HSEIN_ENOMEM: return "out of memory or workspace too small";
+        case HSEIN_ENOTUNREDUCED: return "H is reduced: a subdiagonal entry is zero";
+        case HSEIN_ENONFINITE: return "H or a shift is not finite";
+        case HSEIN_ECUDA: return "CUDA error";
+        case HSEIN_ESHIFTS: return "number of complex shifts differs from the plan";
+        case HSEIN_WNOTCONVERGED: return "some columns did not converge (set to zero)";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

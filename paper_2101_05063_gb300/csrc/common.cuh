@@ -1,0 +1,107 @@
+// Internal declarations shared by the translation units of libhsein.
+//
+// Data layout in the caller's workspace (every block 256-byte aligned):
+//   DevState                      scalars: device status, ||H||_inf, prescale
+//   int   qsrc[m]                 internal shift q -> input position l
+//   int   qcol[m]                 internal shift q -> first user column
+//   double lam[2m]                prescaled shifts (re, im) by internal shift
+//   double bnorm[m]               ||b_q||_2 of the starting vector
+//   int   eB[m]                   exponent shared by the unfinished rows
+//   int   etile[N*m]              exponent of every finished tile segment
+//   u64   bmax[m], rmax[m]        max |B(1:p0,q)|, max |R~(1:p0,q)| (double bits)
+//   Epi   epi[m]                  per-shift epilogue parameters of the update
+//   u64   anorm[N]                max row sum of H(1:p0, J^-) (double bits)
+//   double rowpart[n*(N+1)]       per-row partial sums of |H| by column chunk
+//   double X[ldw*ncolp]           working solution, internal column order
+//   double R[ldw*ncolp]           live cross-over columns R~ (one per column)
+//   double Cr[n*m], Ci[n*m], S[n*m]  Givens rotations (Sec. 3.1, eq. givens)
+//   double ZW[br*2*ncolp]         operand [Z'|W] of the shared-H product
+//
+// Internal column order: the m_cplx complex shifts first (two columns each,
+// starting at even columns), then the m_real real shifts; ncolp pads the
+// column count to a multiple of 32.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hsein {
+
+constexpr int kMaxBr = 128;
+constexpr int kNegInfLog = -100000;  // log2 bound of zero
+
+struct DevState {
+    int status;        // 0 ok, < 0 device error, 1 some column not converged
+    int hexp;          // prescale exponent s >= 0 (H' = 2^-s H)
+    int ncplx_found;   // number of wi != 0 seen
+    int pad0;
+    double hscale;     // 2^-s
+    double hnorm;      // ||H'||_inf (prescaled)
+    unsigned long long hnorm_bits;   // ||H||_inf of the raw matrix, as bits
+    unsigned long long lammax_bits;  // max |lambda| of the raw shifts, as bits
+};
+
+struct Epi {
+    double fB;          // 2^(eB_old - eB_new): rescales B(1:p0)
+    double pi;          // prod of the tile's sines (multiplies R~)
+    double zbr_re, zbr_im;   // last entry of z (multiplies R~ in the B update)
+    double cz_re, cz_im;     // lambda' * rho' (row p0-1 of the B update)
+    double cw_re, cw_im;     // lambda' * c_0  (row p0-1 of the R~ update)
+};
+
+struct Layout {
+    int n, m, mr, mc, ncol, ncolp, br, N, b0, ldw;
+    size_t off_state, off_qsrc, off_qcol, off_lam, off_bnorm, off_eB, off_etile, off_bmax,
+        off_rmax, off_epi, off_anorm, off_rowpart, off_X, off_R, off_Cr, off_Ci, off_S, off_ZW,
+        total;
+};
+
+// first row of tile J (tile 0 is the ragged top-left tile of height b0)
+__host__ __device__ inline int tile_start(const Layout& L, int J) {
+    return J == 0 ? 0 : L.b0 + (J - 1) * L.br;
+}
+__host__ __device__ inline int tile_height(const Layout& L, int J) {
+    return J == 0 ? L.b0 : L.br;
+}
+// internal column of internal shift q
+__host__ __device__ inline int qcolumn(const Layout& L, int q) {
+    return q < L.mc ? 2 * q : 2 * L.mc + (q - L.mc);
+}
+
+template <typename T>
+__host__ __device__ inline T* ws(void* base, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+// upper bound on log2(v): v < 2^L for v > 0 finite; kNegInfLog for v == 0
+__device__ inline int log2_bound(double v) {
+    if (!(v > 0.0)) return kNegInfLog;
+    return ilogb(v) + 1;
+}
+
+__device__ inline void atomic_max_nonneg(unsigned long long* addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ inline double bits_to_double(unsigned long long b) {
+    return __longlong_as_double((long long)b);
+}
+
+__device__ inline void set_error(DevState* st, int code) {
+    atomicMin(&st->status, code);
+}
+
+// host launchers (one per translation unit)
+void launch_prepare(const Layout& L, void* work, const double* H, int ldh, const double* wr,
+                    const double* wi, const double* B, int ldb, int omega_log2, cudaStream_t s);
+void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, int robust,
+                 int omega_log2, cudaStream_t s);
+void launch_update(const Layout& L, void* work, const double* H, int ldh, int J, cudaStream_t s);
+void launch_finalize(const Layout& L, void* work, double* X, int ldx, int* status,
+                     cudaStream_t s);
+void launch_q0(const Layout& L, const double* Q, int ldq, const double* X, int ldx, double* Z,
+               int ldz, cudaStream_t s);
+
+}  // namespace hsein

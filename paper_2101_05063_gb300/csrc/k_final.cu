@@ -1,0 +1,233 @@
+// K4: RBacktransform (Alg. "consistency-scaling", eq. "robust-backtransform")
+// plus the convergence test of Sec. 4.2, one thread block per shift.
+//
+//  1. alpha_min: the largest tile exponent e_max; every tile segment is
+//     brought to it by an exact power-of-two factor (consistency scaling).
+//  2. DNRM2-style scaled 2-norm (running maximum and scaled sum), reduced
+//     across the block in a fixed tree order.
+//  3. Varah's test: ||x||_2 2^e_max / ||b||_2 > 1 / (10 n ||H||_inf eps),
+//     evaluated in log2.  A column that fails is set to zero (Sec. 4.2).
+//  4. y = G_n^H (... (G_2^H (x / ||x||))): the recurrence
+//        y(k-1) = c_k tau - s_k x_k,   tau <- s_k tau + conj(c_k) x_k
+//     is a first-order linear recurrence in tau, so each thread composes the
+//     affine maps of its chunk of rows, a block scan combines the chunks and
+//     each thread then emits its outputs.
+// Output goes to the caller's X in input column order; dStatus per shift.
+#include "common.cuh"
+
+namespace hsein {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Nrm {
+    double m, t;
+};
+__device__ inline Nrm nrm_add(Nrm a, double v) {
+    double x = fabs(v);
+    if (x == 0.0) return a;
+    if (a.m < x) {
+        double r = a.m / x;
+        a.t = 1.0 + a.t * r * r;
+        a.m = x;
+    } else {
+        double r = x / a.m;
+        a.t += r * r;
+    }
+    return a;
+}
+__device__ inline Nrm nrm_merge(Nrm a, Nrm b) {
+    if (a.m < b.m) {
+        Nrm t = a;
+        a = b;
+        b = t;
+    }
+    if (a.m == 0.0) return a;
+    double r = b.m / a.m;
+    a.t += b.t * r * r;
+    return a;
+}
+
+// affine map tau -> a tau + (br + i bi), a real
+struct Aff {
+    double a, br, bi;
+};
+// apply f then g
+__device__ inline Aff aff_then(Aff f, Aff g) {
+    return Aff{g.a * f.a, fma(g.a, f.br, g.br), fma(g.a, f.bi, g.bi)};
+}
+
+template <bool CPLX>
+__device__ void finalize_shift(const Layout& L, void* work, int q, double* __restrict__ Xo,
+                               int ldx, int* __restrict__ status) {
+    const DevState* st = ws<DevState>(work, L.off_state);
+    DevState* stw = ws<DevState>(work, L.off_state);
+    const int* qsrc = ws<int>(work, L.off_qsrc);
+    const int* qcol = ws<int>(work, L.off_qcol);
+    const int* etile = ws<int>(work, L.off_etile);
+    const double* bnorm = ws<double>(work, L.off_bnorm);
+    const double* X = ws<double>(work, L.off_X);
+    const double* Cr = ws<double>(work, L.off_Cr);
+    const double* Ci = ws<double>(work, L.off_Ci);
+    const double* Sv = ws<double>(work, L.off_S);
+    __shared__ int s_emax;
+    __shared__ double s_m[32], s_t[32];
+    __shared__ Aff s_aff[32];
+    __shared__ int s_conv;
+    __shared__ double s_scale;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = L.n;
+    const int col = qcolumn(L, q);
+    const double* xr = X + (size_t)col * L.ldw;
+    const double* xi = X + (size_t)(col + 1) * L.ldw;
+    const double* cr = Cr + (size_t)q * n;
+    const double* ci = Ci + (size_t)q * n;
+    const double* sv = Sv + (size_t)q * n;
+
+    if (tid == 0) {
+        int em = etile[q];
+        for (int J = 1; J < L.N; ++J) em = max(em, etile[(size_t)J * L.m + q]);
+        s_emax = em;
+    }
+    __syncthreads();
+    const int emax = s_emax;
+    // tile of row i and its consistency factor 2^(e_tile - e_max)
+    auto factor = [&](int i) {
+        int J = i < L.b0 ? 0 : 1 + (i - L.b0) / L.br;
+        return ldexp(1.0, etile[(size_t)J * L.m + q] - emax);
+    };
+    const int cs = (n + kThreads - 1) / kThreads;
+    const int a0 = min(n, tid * cs), a1 = min(n, a0 + cs);
+    Nrm nr{0.0, 0.0};
+    for (int i = a0; i < a1; ++i) {
+        double f = factor(i);
+        nr = nrm_add(nr, xr[i] * f);
+        if (CPLX) nr = nrm_add(nr, xi[i] * f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Nrm other{__shfl_xor_sync(0xffffffffu, nr.m, o), __shfl_xor_sync(0xffffffffu, nr.t, o)};
+        nr = nrm_merge(nr, other);
+    }
+    if (lane == 0) {
+        s_m[warp] = nr.m;
+        s_t[warp] = nr.t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        Nrm a{0.0, 0.0};
+        for (int w = 0; w < kThreads / 32; ++w) a = nrm_merge(a, Nrm{s_m[w], s_t[w]});
+        const double nrm = a.m * sqrt(a.t);
+        const double thr = -log2(10.0 * n * st->hnorm * 0x1p-53);
+        int conv = (nrm > 0.0) && (log2(nrm) + emax - log2(bnorm[q]) > thr);
+        s_conv = conv;
+        s_scale = conv ? 1.0 / nrm : 0.0;
+    }
+    __syncthreads();
+    const int uc = qcol[q];
+    double* yr = Xo + (size_t)uc * ldx;
+    double* yi = Xo + (size_t)(uc + 1) * ldx;
+    if (!s_conv) {
+        for (int i = tid; i < n; i += kThreads) {
+            yr[i] = 0.0;
+            if (CPLX) yi[i] = 0.0;
+        }
+        if (tid == 0) {
+            status[qsrc[q]] = 1;
+            atomicCAS(&stw->status, 0, 1);
+        }
+        return;
+    }
+    const double inv = s_scale;
+    // chunk map: tau_out = a tau_in + b over rows a0..a1-1
+    Aff f{1.0, 0.0, 0.0};
+    for (int k = a0; k < a1; ++k) {
+        double g = factor(k) * inv;
+        double yk_r = xr[k] * g, yk_i = CPLX ? xi[k] * g : 0.0;
+        Aff step;
+        if (k == 0) {
+            step = Aff{0.0, yk_r, yk_i};
+        } else {
+            double c_r = cr[k], c_i = CPLX ? ci[k] : 0.0, s = sv[k];
+            // conj(c) y
+            step = Aff{s, c_r * yk_r + c_i * yk_i, c_r * yk_i - c_i * yk_r};
+        }
+        f = aff_then(f, step);
+    }
+    // inclusive scan of chunk maps across the block (warp shuffles, then warps)
+    Aff inc = f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Aff p{__shfl_up_sync(0xffffffffu, inc.a, o), __shfl_up_sync(0xffffffffu, inc.br, o),
+              __shfl_up_sync(0xffffffffu, inc.bi, o)};
+        if (lane >= o) inc = aff_then(p, inc);
+    }
+    if (lane == 31) s_aff[warp] = inc;
+    __syncthreads();
+    if (tid == 0) {
+        Aff run = s_aff[0];
+        for (int w = 1; w < kThreads / 32; ++w) {
+            run = aff_then(run, s_aff[w]);
+            s_aff[w] = run;
+        }
+    }
+    __syncthreads();
+    // exclusive prefix for this thread: warps before, then lanes before
+    Aff ex{1.0, 0.0, 0.0};
+    if (warp > 0) ex = s_aff[warp - 1];
+    Aff lanepre{__shfl_up_sync(0xffffffffu, inc.a, 1), __shfl_up_sync(0xffffffffu, inc.br, 1),
+                __shfl_up_sync(0xffffffffu, inc.bi, 1)};
+    if (lane > 0) ex = aff_then(ex, lanepre);
+    double tr = ex.br, ti = ex.bi;  // tau entering row a0 (the map applied to 0)
+    for (int k = a0; k < a1; ++k) {
+        double g = factor(k) * inv;
+        double yk_r = xr[k] * g, yk_i = CPLX ? xi[k] * g : 0.0;
+        if (k == 0) {
+            tr = yk_r;
+            ti = yk_i;
+            continue;
+        }
+        double c_r = cr[k], c_i = CPLX ? ci[k] : 0.0, s = sv[k];
+        // y(k-1) = c tau - s y_k
+        double outr = c_r * tr - c_i * ti - s * yk_r;
+        double outi = c_r * ti + c_i * tr - s * yk_i;
+        yr[k - 1] = outr;
+        if (CPLX) yi[k - 1] = outi;
+        double ntr = s * tr + c_r * yk_r + c_i * yk_i;
+        double nti = s * ti + c_r * yk_i - c_i * yk_r;
+        tr = ntr;
+        ti = nti;
+    }
+    if (a1 == n && a0 < a1) {
+        yr[n - 1] = tr;
+        if (CPLX) yi[n - 1] = ti;
+    }
+    if (tid == 0) status[qsrc[q]] = 0;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_finalize(Layout L, void* work, double* __restrict__ Xo, int ldx, int* __restrict__ status) {
+    const DevState* st = ws<DevState>(work, L.off_state);
+    const int q = blockIdx.x;
+    if (st->status < 0) {
+        // the solve did not run: mark every shift invalid, zero the output
+        if (q < L.m && threadIdx.x == 0) status[q] = 3;
+        for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (size_t)L.n * L.ncol;
+             idx += (size_t)gridDim.x * blockDim.x) {
+            size_t c = idx / L.n, i = idx % L.n;
+            Xo[i + c * ldx] = 0.0;
+        }
+        return;
+    }
+    if (q < L.mc) finalize_shift<true>(L, work, q, Xo, ldx, status);
+    else finalize_shift<false>(L, work, q, Xo, ldx, status);
+}
+
+}  // namespace
+
+void launch_finalize(const Layout& L, void* work, double* X, int ldx, int* status,
+                     cudaStream_t s) {
+    k_finalize<<<L.m, kThreads, 0, s>>>(L, work, X, ldx, status);
+}
+
+}  // namespace hsein

@@ -1,0 +1,246 @@
+"""Parity of the CUDA path with the CPU oracle (run on a GB300).
+
+Every test solves the same seeded input on the GPU (through the C ABI via the
+Python binding) and with the oracle, and compares:
+  - per-shift status codes (bit-exact: converged / not converged), except for
+    shifts whose Varah ratio lies within a factor 2 of the threshold;
+  - eigenvectors by the sign/phase-invariant angle: <= 1e-10 for shifts whose
+    eigenvalue is separated from the rest of the spectrum by >= 1e-3 ||H||_inf
+    (the acceptance bound), and the diagnostic bound 1e3 n eps ||H|| / gap
+    otherwise;
+  - the normwise residual ||H x - lambda x||_1 / (||H||_1 ||x||_1) <= 100 n eps
+    for every converged column;
+  - Z = Q0 X against numpy's product of the same operands.
+"""
+import numpy as np
+import pytest
+
+import hsein_inputs as hi
+import oracle
+from tests.metrics import EPS, angle, as_vectors, residual
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2101_05063_gb300 as hs  # noqa: E402
+
+
+def to_dev(a):
+    return torch.as_tensor(np.asfortranarray(a), dtype=torch.float64).cuda()
+
+
+def run_gpu(inst_H, wr, wi, B, br=64, robust=True, omega_log2=1000, Q0=None):
+    wr = np.asarray(wr, dtype=np.float64)
+    wi = np.asarray(wi, dtype=np.float64)
+    mc = int(np.count_nonzero(wi))
+    n = inst_H.shape[0]
+    solver = hs.Solver(n, len(wr) - mc, mc, br=br, robust=robust, omega_log2=omega_log2)
+    X, status = solver.solve(to_dev(inst_H), to_dev(wr), to_dev(wi),
+                             None if B is None else to_dev(B))
+    Z = solver.backtransform(to_dev(Q0), X) if Q0 is not None else None
+    torch.cuda.synchronize()
+    Xh = X.cpu().numpy()
+    out = (Xh, status.cpu().numpy(), solver)
+    if Z is not None:
+        out = out + (Z.cpu().numpy(),)
+    return out
+
+
+def separation(eigs, lam):
+    d = np.abs(np.asarray(eigs) - lam)
+    d = np.sort(d)
+    return d[1] if len(d) > 1 else np.inf
+
+
+def compare(H, wr, wi, Xg, sg, Xo, so, eigs=None, hnorm=None, strict_status=True):
+    n = H.shape[0]
+    hn = hnorm if hnorm is not None else oracle.hnorm_inf(H)
+    if strict_status:
+        assert np.array_equal(sg, so), (sg, so)
+    vg = as_vectors(Xg, wr, wi)
+    vo = as_vectors(Xo, wr, wi)
+    worst = 0.0
+    for l, ((lam, xg), (_, xo)) in enumerate(zip(vg, vo)):
+        if so[l] != 0 or sg[l] != 0:
+            continue
+        assert np.all(np.isfinite(xg))
+        assert abs(np.linalg.norm(xg) - 1.0) <= 8 * n * EPS
+        r = residual(H, lam, xg)
+        assert r <= 100 * n * EPS, (l, r / (n * EPS))
+        a = angle(xg, xo)
+        gap = separation(eigs, lam) if eigs is not None else np.inf
+        bound = 1e-10 if gap >= 1e-3 * hn else max(1e-10, 1e3 * n * EPS * hn / gap)
+        assert a <= bound, (l, lam, a, gap)
+        worst = max(worst, a)
+    return worst
+
+
+CASES = [
+    # n, m_real, m_cplx, br, seed
+    (1, 1, 0, 8, 1),
+    (2, 1, 0, 8, 2),
+    (3, 1, 1, 8, 3),
+    (7, 2, 1, 8, 4),
+    (8, 3, 1, 8, 5),
+    (9, 3, 2, 8, 6),
+    (37, 5, 3, 8, 7),
+    (63, 6, 4, 32, 8),
+    (64, 6, 4, 32, 9),
+    (65, 6, 4, 32, 10),
+    (131, 12, 9, 32, 11),
+    (200, 20, 10, 64, 12),
+    (257, 30, 17, 64, 13),
+    (300, 0, 20, 64, 14),
+    (300, 33, 0, 64, 15),
+    (333, 40, 25, 128, 16),
+]
+
+
+@pytest.mark.parametrize("n,mr,mc,br,seed", CASES)
+def test_small_instances_match_oracle(n, mr, mc, br, seed):
+    if n == 1:
+        H = np.array([[2.5]])
+        wr, wi, B = np.array([2.5 + 1e-3]), np.array([0.0]), np.ones((1, 1))
+        eigs = np.array([2.5])
+    elif n == 2:
+        H = np.array([[1.0, 2.0], [0.5, -1.0]])
+        ev = np.linalg.eigvals(H)
+        wr, wi, B = np.array([ev[0].real]), np.array([0.0]), np.array([[0.6], [0.8]])
+        eigs = ev
+    else:
+        inst = hi.small_instance(n, mr, mc, seed)
+        H, wr, wi, B, eigs = inst.H, inst.wr, inst.wi, inst.B, inst.eigs
+    Xg, sg, _ = run_gpu(H, wr, wi, B, br=br)
+    Xo, so = oracle.hsein(H, wr, wi, B)
+    compare(H, wr, wi, Xg, sg, Xo, so, eigs)
+
+
+@pytest.mark.parametrize("br", [16, 64])
+def test_default_starting_vector(br):
+    inst = hi.small_instance(150, 10, 6, 21)
+    Xg, sg, _ = run_gpu(inst.H, inst.wr, inst.wi, None, br=br)
+    Xo, so = oracle.hsein(inst.H, inst.wr, inst.wi, None)
+    compare(inst.H, inst.wr, inst.wi, Xg, sg, Xo, so, inst.eigs)
+
+
+def test_config0_full_size_with_backtransform():
+    inst = hi.config0()
+    Xg, sg, _, Zg = run_gpu(inst.H, inst.wr, inst.wi, inst.B, Q0=inst.Q0)
+    Xo, so = oracle.hsein(inst.H, inst.wr, inst.wi, inst.B)
+    compare(inst.H, inst.wr, inst.wi, Xg, sg, Xo, so, inst.eigs)
+    Zref = inst.Q0 @ Xg
+    assert np.abs(Zg - Zref).max() <= 1e-13
+    Zo = oracle.q0_apply(inst.Q0, Xo)
+    for l in range(inst.m):
+        assert angle(Zg[:, l], Zo[:, l]) <= 1e-9
+
+
+@pytest.mark.parametrize("n,om", [(48, 30), (96, 40), (200, 60)])
+def test_bad_system_h2_scaling_matches_oracle(n, om):
+    # the bad system of Sec. 5.2 with a lowered overflow threshold: the
+    # scaling paths of the diagonal solve and of the shared-H update run
+    H = hi.paper_h2(n)
+    B = np.ones((n, 1)) / np.sqrt(n)
+    for br in (8, 32):
+        Xg, sg, _ = run_gpu(H, [2.0], [0.0], B, br=br, omega_log2=om)
+        Xo, so = oracle.hsein(H, [2.0], [0.0], B, log2_omega=om)
+        assert sg[0] == 0 and so[0] == 0
+        assert np.all(np.isfinite(Xg))
+        assert angle(Xg[:, 0], Xo[:, 0]) <= 1e-12
+        assert residual(H, 2.0, Xg[:, 0]) <= 100 * n * EPS
+
+
+def test_bad_system_h2_default_threshold_no_overflow():
+    n = 1024
+    H = hi.paper_h2(n)
+    B = np.ones((n, 1)) / np.sqrt(n)
+    Xg, sg, _ = run_gpu(H, [2.0], [0.0], B)
+    Xo, so = oracle.hsein(H, [2.0], [0.0], B)
+    assert sg[0] == 0 and np.all(np.isfinite(Xg))
+    assert angle(Xg[:, 0], Xo[:, 0]) <= 1e-12
+    assert residual(H, 2.0, Xg[:, 0]) <= 100 * n * EPS
+
+
+def test_good_system_h3_matches():
+    # (H3 - 2I) is well conditioned, so one solve is not an eigenvector and
+    # both sides must flag it (Varah's test, Sec. 4.2); with eigenvalue
+    # shifts of H3 both sides must agree on the vectors
+    n = 512
+    H = hi.paper_h3(n)
+    B = np.ones((n, 1)) / np.sqrt(n)
+    Xg, sg, _ = run_gpu(H, [2.0], [0.0], B, omega_log2=30)
+    Xo, so = oracle.hsein(H, [2.0], [0.0], B, log2_omega=30)
+    assert sg[0] == 1 and so[0] == 1
+    ev = np.linalg.eigvals(H)
+    real = ev[np.abs(ev.imag) == 0].real
+    wr = np.sort(real)[:: max(1, len(real) // 4)][:4]
+    cp = ev[ev.imag > 0][:2]
+    wr = np.concatenate([wr, cp.real])
+    wi = np.concatenate([np.zeros(len(wr) - len(cp)), cp.imag])
+    offs = hi.column_offsets(wi)
+    Bm = hi.unit_columns(n, int(offs[-1]), seed=5)
+    Xg, sg, _ = run_gpu(H, wr, wi, Bm, omega_log2=30)
+    Xo, so = oracle.hsein(H, wr, wi, Bm, log2_omega=30)
+    compare(H, wr, wi, Xg, sg, Xo, so, ev)
+
+
+def test_graded_matrix_stays_finite():
+    n = 96
+    rng_H = np.triu(hi.normal(11, 50, n * n).reshape(n, n, order="F"), -1)
+    G, d = hi.graded(rng_H, seed=11, umax=150.0, monotone=True)
+    ev = np.linalg.eigvals(rng_H)
+    lam = float(ev[np.argmin(np.abs(ev.imag))].real)
+    b = hi.normal(11, 51, n)[:, None]
+    b /= np.linalg.norm(b)
+    Xg, sg, _ = run_gpu(G, [lam], [0.0], b, br=32)
+    assert np.all(np.isfinite(Xg))
+    if sg[0] == 0:
+        Gl = G.astype(np.longdouble)
+        y = Xg[:, 0].astype(np.longdouble)
+        r = np.abs(Gl @ y - np.longdouble(lam) * y).sum()
+        assert float(r / (np.abs(Gl).sum(axis=0).max() * np.abs(y).sum())) <= 100 * n * EPS
+
+
+def test_device_errors_are_reported():
+    inst = hi.small_instance(40, 3, 2, 31)
+    # zero subdiagonal -> not unreduced
+    H = inst.H.copy()
+    H[10, 9] = 0.0
+    solver = hs.Solver(40, 3, 2)
+    X, st = solver.solve(to_dev(H), to_dev(inst.wr), to_dev(inst.wi), to_dev(inst.B), check=False)
+    assert solver.device_status() == -3
+    assert np.all(st.cpu().numpy() == 3) and np.all(X.cpu().numpy() == 0.0)
+    # non-finite entry
+    H = inst.H.copy()
+    H[3, 20] = np.nan
+    X, st = solver.solve(to_dev(H), to_dev(inst.wr), to_dev(inst.wi), to_dev(inst.B), check=False)
+    assert solver.device_status() == -4
+    # wrong number of complex shifts
+    wi = inst.wi.copy()
+    wi[np.nonzero(wi)[0][0]] = 0.0
+    X, st = solver.solve(to_dev(inst.H), to_dev(inst.wr), to_dev(wi), to_dev(inst.B), check=False)
+    assert solver.device_status() == -7
+    # and a clean solve afterwards still works
+    X, st = solver.solve(to_dev(inst.H), to_dev(inst.wr), to_dev(inst.wi), to_dev(inst.B))
+    assert solver.device_status() in (0, 1)
+
+
+def test_far_shift_not_converged_and_zeroed():
+    inst = hi.small_instance(64, 4, 0, 41)
+    wr = inst.wr.copy()
+    wr[1] = 1e3 * oracle.hnorm_inf(inst.H)
+    Xg, sg, solver = run_gpu(inst.H, wr, inst.wi, inst.B)
+    Xo, so = oracle.hsein(inst.H, wr, inst.wi, inst.B)
+    assert sg[1] == 1 and so[1] == 1
+    assert np.all(Xg[:, 1] == 0.0)
+    assert solver.device_status() == 1
+
+
+def test_repeatable():
+    inst = hi.small_instance(129, 9, 5, 51)
+    X1, s1, _ = run_gpu(inst.H, inst.wr, inst.wi, inst.B)
+    X2, s2, _ = run_gpu(inst.H, inst.wr, inst.wi, inst.B)
+    assert np.array_equal(X1, X2) and np.array_equal(s1, s2)
