@@ -109,6 +109,28 @@ hsein_status hsein_solve(hsein_plan_t plan, const double *dH, int ldh,
                          int *dStatus, void *dWork, size_t work_bytes, void *stream);
 
 /*
+ * hsein_solve without a workspace argument, for callers that cannot allocate
+ * device memory (code running during CUDA stream capture, plug-ins whose host
+ * framework owns all device memory, real-time paths that must not allocate).
+ * The paper has no counterpart: this is an interface convenience.
+ *   The workspace is a fixed 16 MiB array in the library's device memory,
+ *   present on every device that loads the library until the process exits.
+ *   Plans whose workspace (hsein_plan's *workspace_bytes) exceeds 16 MiB are
+ *   rejected with HSEIN_ENOMEM; nothing is allocated, here or later.
+ *   The first call on a device looks up the array's device address (no
+ *   allocation); make that first call before any stream capture on the device.
+ *   All calls share the array: the solve re-initializes every value it reads,
+ *   but calls whose work overlaps on the GPU (other streams, other threads)
+ *   race and must be serialized by the caller.  Device-side errors show in
+ *   dStatus (every entry HSEIN_COL_INVALID); the other arguments and results
+ *   are those of hsein_solve.
+ */
+hsein_status hsein_solve_noalloc(hsein_plan_t plan, const double *dH, int ldh,
+                                 const double *dWr, const double *dWi,
+                                 const double *dB, int ldb, double *dX, int ldx,
+                                 int *dStatus, void *stream);
+
+/*
  * z_l = Q0 x_l for every column (Sec. 1: H = Q0^T A Q0 maps eigenvectors of H
  * to eigenvectors of A).  dQ0 n x n (ldq >= n), dX n x ncol (ldx >= n), dZ
  * n x ncol output (ldz >= n, may not alias dX).  dWork as for hsein_solve

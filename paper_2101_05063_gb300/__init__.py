@@ -21,7 +21,7 @@ from . import build as _build
 
 __all__ = [
     "HseinError", "HseinOptions", "load", "hsein_default_options", "hsein_plan", "hsein_solve",
-    "hsein_backtransform", "hsein_plan_sync_status", "hsein_plan_info", "hsein_plan_destroy",
+    "hsein_solve_noalloc", "hsein_backtransform", "hsein_plan_sync_status", "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
     "STATUS", "PHASES",
 ]
@@ -67,6 +67,8 @@ def load(build_if_missing=True):
                                ctypes.POINTER(sz)]
     lib.hsein_solve.restype = ctypes.c_int
     lib.hsein_solve.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, vp, sz, vp]
+    lib.hsein_solve_noalloc.restype = ctypes.c_int
+    lib.hsein_solve_noalloc.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, vp]
     lib.hsein_backtransform.restype = ctypes.c_int
     lib.hsein_backtransform.argtypes = [vp, dp, ip, dp, ip, dp, ip, vp, sz, vp]
     lib.hsein_plan_sync_status.restype = ctypes.c_int
@@ -108,6 +110,13 @@ def hsein_solve(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, dWork, work_
     """Device pointers are integers (e.g. tensor.data_ptr()); dB may be 0."""
     return load().hsein_solve(plan, dH, ldh, dWr, dWi, dB or None, ldb, dX, ldx, dStatus, dWork,
                               work_bytes, stream or None)
+
+
+def hsein_solve_noalloc(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, stream):
+    """hsein_solve on the library's fixed device array instead of a caller
+    workspace: for callers that cannot allocate device memory."""
+    return load().hsein_solve_noalloc(plan, dH, ldh, dWr, dWi, dB or None, ldb, dX, ldx, dStatus,
+                                      stream or None)
 
 
 def hsein_backtransform(plan, dQ0, ldq, dX, ldx, dZ, ldz, dWork, work_bytes, stream):
