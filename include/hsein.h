@@ -63,7 +63,8 @@ enum {
 
 typedef struct {
     int br;         /* tile height b_r (Sec. 3.2), 8..128; 0 = default (64)                 */
-    int precision;  /* 0 = FP64 products (the only mode of this version)                     */
+    int precision;  /* 0 = FP64 products; 1 = split-precision products on the BF16 tensor    */
+                    /*     cores with FP64 recombination (z = Q0 x), see hsein_backtransform  */
     int robust;     /* 1 = overflow protection (default); 0 = off, for tests that show       */
                     /*     what the protection prevents                                      */
     int omega_log2; /* stored solution entries stay below 2^omega_log2; 0 = default (1000).  */
@@ -135,6 +136,12 @@ hsein_status hsein_solve_noalloc(hsein_plan_t plan, const double *dH, int ldh,
  * to eigenvectors of A).  dQ0 n x n (ldq >= n), dX n x ncol (ldx >= n), dZ
  * n x ncol output (ldz >= n, may not alias dX).  dWork as for hsein_solve
  * (the same buffer may be reused after the solve).  Stream-ordered.
+ * precision 0: an FP64 product.  precision 1: every row of Q0 and column of
+ * X is scaled by a power of two and cut into seven 8-bit digits, the digit
+ * products with weight above the FP64 rounding level run on the BF16 tensor
+ * cores with exact integer accumulation of the leading terms, and the result
+ * is recombined in FP64 (error comparable to an FP64 product); dWork is used
+ * and must be the size hsein_plan reported.
  */
 hsein_status hsein_backtransform(hsein_plan_t plan, const double *dQ0, int ldq,
                                  const double *dX, int ldx, double *dZ, int ldz,

@@ -194,7 +194,8 @@ class Solver:
     used in place when already column-major) and run on the current stream.
     """
 
-    def __init__(self, n, m_real, m_cplx, br=64, robust=True, omega_log2=1000, device=None):
+    def __init__(self, n, m_real, m_cplx, br=64, robust=True, omega_log2=1000, precision=0,
+                 device=None):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -203,6 +204,7 @@ class Solver:
             opt.br = int(br)
             opt.robust = int(bool(robust))
             opt.omega_log2 = int(omega_log2)
+            opt.precision = int(precision)
             self.plan, self.work_bytes = hsein_plan(n, m_real, m_cplx, opt)
         self.n, self.m_real, self.m_cplx = int(n), int(m_real), int(m_cplx)
         self.m = self.m_real + self.m_cplx

@@ -13,6 +13,7 @@
 // Sec. 4.4, and must group shifts because of it).
 #include "../../include/hsein.h"
 #include "common.cuh"
+#include "ozaki.cuh"
 
 #include <cstdint>
 #include <cstdlib>
@@ -41,7 +42,7 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-void make_layout(Layout* L, int n, int mr, int mc, int br) {
+void make_layout(Layout* L, int n, int mr, int mc, int br, int precision) {
     L->n = n;
     L->mr = mr;
     L->mc = mc;
@@ -77,6 +78,10 @@ void make_layout(Layout* L, int n, int mr, int mc, int br) {
     L->off_Ci = take(sizeof(double) * nn * (size_t)(mc > 0 ? mc : 1));
     L->off_S = take(sizeof(double) * nn * m);
     L->off_ZW = take(sizeof(double) * (size_t)br * 2 * L->ncolp);
+    // buffers of the split-precision backtransform follow the solve's state,
+    // which stays readable (hsein_plan_sync_status) after the backtransform
+    L->off_oz = o;
+    if (precision == 1) o = align256(o + hsein::ozq0_workspace_bytes(n, L->ncol));
     L->total = o;
 }
 
@@ -139,15 +144,16 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         if (opt->omega_log2 != 0) o.omega_log2 = opt->omega_log2;
     }
     if (o.br < 8 || o.br > hsein::kMaxBr) return HSEIN_EARG;
-    if (o.precision != 0) return HSEIN_EARG;
+    if (o.precision != 0 && o.precision != 1) return HSEIN_EARG;
     if (o.robust != 0 && o.robust != 1) return HSEIN_EARG;
     if (o.omega_log2 < 16 || o.omega_log2 > 1000) return HSEIN_EARG;
     hsein_plan_s* p = new (std::nothrow) hsein_plan_s;
     if (!p) return HSEIN_ENOMEM;
-    make_layout(&p->L, n, m_real, m_cplx, o.br);
+    make_layout(&p->L, n, m_real, m_cplx, o.br, o.precision);
     p->opt = o;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
-        hsein::diag_configure(o.br) != cudaSuccess || hsein::update_configure(o.br) != cudaSuccess) {
+        hsein::diag_configure(o.br) != cudaSuccess || hsein::update_configure(o.br) != cudaSuccess ||
+        hsein::ozaki_configure() != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return HSEIN_ECUDA;
@@ -213,11 +219,16 @@ hsein_status hsein_backtransform(hsein_plan_t plan, const double* dQ0, int ldq, 
     const Layout& L = plan->L;
     if (!dQ0 || ldq < L.n || !dX || ldx < L.n || !dZ || ldz < L.n) return HSEIN_EARG;
     if ((const void*)dZ == (const void*)dX || (const void*)dZ == (const void*)dQ0) return HSEIN_EARG;
-    (void)dWork;
-    (void)work_bytes;
-    {
-        PhaseScope ps(plan, 4, static_cast<cudaStream_t>(stream));
-        hsein::launch_q0(L, dQ0, ldq, dX, ldx, dZ, ldz, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->opt.precision == 1) {
+        if (!dWork || !aligned256(dWork)) return HSEIN_EARG;
+        if (work_bytes < L.total) return HSEIN_ENOMEM;
+        PhaseScope ps(plan, 4, s);
+        hsein::launch_ozaki_q0(L.n, L.ncol, dQ0, ldq, dX, ldx, dZ, ldz,
+                               static_cast<char*>(dWork) + L.off_oz, s);
+    } else {
+        PhaseScope ps(plan, 4, s);
+        hsein::launch_q0(L, dQ0, ldq, dX, ldx, dZ, ldz, s);
     }
     if (cudaGetLastError() != cudaSuccess) return HSEIN_ECUDA;
     return HSEIN_OK;

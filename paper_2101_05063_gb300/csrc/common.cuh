@@ -54,7 +54,7 @@ struct Layout {
     int n, m, mr, mc, ncol, ncolp, br, N, b0, ldw;
     size_t off_state, off_qsrc, off_qcol, off_lam, off_bnorm, off_eB, off_etile, off_bmax,
         off_rmax, off_epi, off_anorm, off_rowpart, off_X, off_R, off_Cr, off_Ci, off_S, off_ZW,
-        total;
+        off_oz, total;
 };
 
 // first row of tile J (tile 0 is the ragged top-left tile of height b0)

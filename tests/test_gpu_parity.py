@@ -244,3 +244,43 @@ def test_repeatable():
     X1, s1, _ = run_gpu(inst.H, inst.wr, inst.wi, inst.B)
     X2, s2, _ = run_gpu(inst.H, inst.wr, inst.wi, inst.B)
     assert np.array_equal(X1, X2) and np.array_equal(s1, s2)
+
+
+def _ld_product(Q, X):
+    return (np.asarray(Q, dtype=np.longdouble) @ np.asarray(X, dtype=np.longdouble))
+
+
+@pytest.mark.parametrize("n,ncol,graded", [(512, 64, False), (333, 37, False), (257, 20, True)])
+def test_split_precision_backtransform_accuracy(n, ncol, graded):
+    # z = Q0 x with the BF16 digit products must be as accurate as the FP64
+    # product, measured against a long-double product of the same operands
+    Q = hi.haar_orthogonal(n, 3)
+    X = hi.unit_columns(n, ncol, seed=4)
+    if graded:
+        # rows and columns of very different scales exercise the exponents
+        Q = Q * (10.0 ** hi.uniform(5, 1, n, -30, 30))[:, None]
+        X = X * (10.0 ** hi.uniform(6, 1, ncol, -200, 200))[None, :]
+        X[:, 3] = 0.0
+    dQ, dX = to_dev(Q), to_dev(X)
+    s64 = hs.Solver(n, ncol, 0, precision=0)
+    soz = hs.Solver(n, ncol, 0, precision=1)
+    Z64 = s64.backtransform(dQ, dX).cpu().numpy()
+    Zoz = soz.backtransform(dQ, dX).cpu().numpy()
+    Zex = _ld_product(Q, X)
+    scale = (np.abs(Q).max(axis=1)[:, None] * np.abs(X).max(axis=0)[None, :]).astype(np.longdouble)
+    scale[scale == 0] = 1
+    e64 = float(np.max(np.abs(Z64 - Zex) / scale))
+    eoz = float(np.max(np.abs(Zoz - Zex) / scale))
+    assert np.all(Zoz[:, 3] == 0.0) if graded else True
+    assert eoz <= max(4 * e64, 8 * n * EPS), (eoz, e64)
+
+
+def test_split_precision_pipeline_matches_oracle():
+    inst = hi.config0()
+    solver = hs.Solver(inst.n, inst.m_real, inst.m_cplx, precision=1)
+    X, st = solver.solve(to_dev(inst.H), to_dev(inst.wr), to_dev(inst.wi), to_dev(inst.B))
+    Z = solver.backtransform(to_dev(inst.Q0), X).cpu().numpy()
+    Xo, so = oracle.hsein(inst.H, inst.wr, inst.wi, inst.B)
+    Zo = oracle.q0_apply(inst.Q0, Xo)
+    for l in range(inst.m):
+        assert angle(Z[:, l], Zo[:, l]) <= 1e-9
