@@ -23,6 +23,7 @@
 namespace hsein {
 cudaError_t diag_configure(int br);
 cudaError_t update_configure(int br);
+cudaError_t update_oz_configure();
 }  // namespace hsein
 
 using hsein::Layout;
@@ -78,6 +79,14 @@ void make_layout(Layout* L, int n, int mr, int mc, int br, int precision) {
     L->off_Ci = take(sizeof(double) * nn * (size_t)(mc > 0 ? mc : 1));
     L->off_S = take(sizeof(double) * nn * m);
     L->off_ZW = take(sizeof(double) * (size_t)br * 2 * L->ncolp);
+    L->oz = precision == 1 ? 1 : 0;
+    {
+        const size_t P = L->oz ? hsein::oz_update_hd_elems(*L) : 0;
+        L->off_hd = take(2 * (size_t)hsein::oz::kS * br * P);
+        L->off_he = take(sizeof(int) * P);
+        L->off_zwd = take(L->oz ? 2 * (size_t)hsein::oz::kS * 2 * L->ncolp * br : 0);
+        L->off_zwf = take(L->oz ? sizeof(int) * 2 * (size_t)L->ncolp : 0);
+    }
     // buffers of the split-precision backtransform follow the solve's state,
     // which stays readable (hsein_plan_sync_status) after the backtransform
     L->off_oz = o;
@@ -145,6 +154,7 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
     }
     if (o.br < 8 || o.br > hsein::kMaxBr) return HSEIN_EARG;
     if (o.precision != 0 && o.precision != 1) return HSEIN_EARG;
+    if (o.precision == 1 && o.br != 64) return HSEIN_EARG;  // digit tiles are 64 wide
     if (o.robust != 0 && o.robust != 1) return HSEIN_EARG;
     if (o.omega_log2 < 16 || o.omega_log2 > 1000) return HSEIN_EARG;
     hsein_plan_s* p = new (std::nothrow) hsein_plan_s;
@@ -153,7 +163,7 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
     p->opt = o;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         hsein::diag_configure(o.br) != cudaSuccess || hsein::update_configure(o.br) != cudaSuccess ||
-        hsein::ozaki_configure() != cudaSuccess) {
+        hsein::ozaki_configure() != cudaSuccess || hsein::update_oz_configure() != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return HSEIN_ECUDA;
@@ -191,6 +201,7 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
     {
         PhaseScope ps(plan, 0, s);
         hsein::launch_prepare(L, dWork, dH, ldh, dWr, dWi, dB, ldb, om, s);
+        if (L.oz) hsein::launch_split_h(L, dWork, dH, ldh, s);
     }
     for (int J = L.N - 1; J >= 1; --J) {
         {
@@ -198,7 +209,10 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
             hsein::launch_diag(L, dWork, dH, ldh, J, robust, om, s);
         }
         PhaseScope ps(plan, 2, s);
-        hsein::launch_update(L, dWork, dH, ldh, J, s);
+        if (L.oz)
+            hsein::launch_update_oz(L, dWork, J, s);
+        else
+            hsein::launch_update(L, dWork, dH, ldh, J, s);
     }
     {
         PhaseScope ps(plan, 1, s);

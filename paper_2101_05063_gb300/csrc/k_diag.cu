@@ -29,6 +29,7 @@
 // all three linear updates of eq. "robust-update"), and [Z'|W] plus the
 // epilogue constants are written for the shared-H product (k_update).
 #include "common.cuh"
+#include "ozaki.cuh"
 
 namespace hsein {
 namespace {
@@ -372,16 +373,44 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
     __syncwarp();
     const double fz = s_s[0];
     const size_t ldzw = 2 * (size_t)L.ncolp;
-    for (int k = lane; k < bt; k += 32) {
-        double* row = ZW + (size_t)k * ldzw + 2 * (size_t)col;
-        if (CPLX) {
-            row[0] = s_zr[k] * fz;
-            row[1] = s_cr[k] * hscale;
-            row[2] = s_zi[k] * fz;
-            row[3] = s_ci[k] * hscale;
-        } else {
-            row[0] = s_zr[k] * fz;
-            row[1] = s_cr[k] * hscale;
+    if (!L.oz) {
+        for (int k = lane; k < bt; k += 32) {
+            double* row = ZW + (size_t)k * ldzw + 2 * (size_t)col;
+            if (CPLX) {
+                row[0] = s_zr[k] * fz;
+                row[1] = s_cr[k] * hscale;
+                row[2] = s_zi[k] * fz;
+                row[3] = s_ci[k] * hscale;
+            } else {
+                row[0] = s_zr[k] * fz;
+                row[1] = s_cr[k] * hscale;
+            }
+        }
+    } else {
+        // [Z'|W] as BF16 digits with one exponent per product column
+        __nv_bfloat16* zd = ws<__nv_bfloat16>(work, L.off_zwd);
+        int* zf = ws<int>(work, L.off_zwf);
+        const int ncols = CPLX ? 4 : 2;
+        for (int cc = 0; cc < ncols; ++cc) {
+            const double* src = (cc & 1) ? ((cc & 2) ? s_ci : s_cr) : ((cc & 2) ? s_zi : s_zr);
+            const double f = (cc & 1) ? hscale : fz;
+            double v0 = lane < bt ? src[lane] * f : 0.0;
+            double v1 = lane + 32 < bt ? src[lane + 32] * f : 0.0;
+            double m = warp_max(fmax(fabs(v0), fabs(v1)));
+            const int e = oz::scale_exponent(m);
+            const int gc = 2 * col + cc;
+            if (lane == 0) zf[gc] = e;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = lane + 32 * h;
+                if (k < br) {
+                    int d[oz::kS];
+                    oz::split_digits(h ? v1 : v0, e, d);
+#pragma unroll
+                    for (int i = 0; i < oz::kS; ++i)
+                        zd[((size_t)i * ldzw + gc) * br + k] = __float2bfloat16_rn((float)d[i]);
+                }
+            }
         }
     }
 }

@@ -28,10 +28,11 @@ def c1():
     return hi.config1()
 
 
-def test_config1_full_size(c1):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config1_full_size(c1, precision):
     inst = c1
     n = inst.n
-    solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=64)
+    solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=64, precision=precision)
     dH = to_dev(inst.H)
     X, status = solver.solve(dH, to_dev(inst.wr), to_dev(inst.wi), to_dev(inst.B))
     Z = solver.backtransform(to_dev(inst.Q0), X)

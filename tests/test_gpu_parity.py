@@ -32,12 +32,13 @@ def to_dev(a):
     return torch.as_tensor(np.asfortranarray(a), dtype=torch.float64).cuda()
 
 
-def run_gpu(inst_H, wr, wi, B, br=64, robust=True, omega_log2=1000, Q0=None):
+def run_gpu(inst_H, wr, wi, B, br=64, robust=True, omega_log2=1000, Q0=None, precision=0):
     wr = np.asarray(wr, dtype=np.float64)
     wi = np.asarray(wi, dtype=np.float64)
     mc = int(np.count_nonzero(wi))
     n = inst_H.shape[0]
-    solver = hs.Solver(n, len(wr) - mc, mc, br=br, robust=robust, omega_log2=omega_log2)
+    solver = hs.Solver(n, len(wr) - mc, mc, br=br, robust=robust, omega_log2=omega_log2,
+                       precision=precision)
     X, status = solver.solve(to_dev(inst_H), to_dev(wr), to_dev(wi),
                              None if B is None else to_dev(B))
     Z = solver.backtransform(to_dev(Q0), X) if Q0 is not None else None
@@ -284,3 +285,28 @@ def test_split_precision_pipeline_matches_oracle():
     Zo = oracle.q0_apply(inst.Q0, Xo)
     for l in range(inst.m):
         assert angle(Z[:, l], Zo[:, l]) <= 1e-9
+
+
+SPLIT_CASES = [(65, 6, 4, 17), (131, 12, 9, 18), (257, 30, 17, 19), (300, 0, 20, 20), (300, 33, 0, 21),
+               (520, 40, 25, 22)]
+
+
+@pytest.mark.parametrize("n,mr,mc,seed", SPLIT_CASES)
+def test_split_precision_small_instances_match_oracle(n, mr, mc, seed):
+    # the shared-H update and the backtransform on BF16 digit products
+    inst = hi.small_instance(n, mr, mc, seed)
+    Xg, sg, _, Zg = run_gpu(inst.H, inst.wr, inst.wi, inst.B, precision=1, Q0=inst.Q0)
+    Xo, so = oracle.hsein(inst.H, inst.wr, inst.wi, inst.B)
+    compare(inst.H, inst.wr, inst.wi, Xg, sg, Xo, so, inst.eigs)
+    assert np.abs(Zg - inst.Q0 @ Xg).max() <= 1e-13
+
+
+@pytest.mark.parametrize("n,om", [(200, 60), (1024, 1000)])
+def test_split_precision_bad_system_h2(n, om):
+    H = hi.paper_h2(n)
+    B = np.ones((n, 1)) / np.sqrt(n)
+    Xg, sg, _ = run_gpu(H, [2.0], [0.0], B, omega_log2=om, precision=1)
+    Xo, so = oracle.hsein(H, [2.0], [0.0], B, log2_omega=om)
+    assert sg[0] == 0 and so[0] == 0 and np.all(np.isfinite(Xg))
+    assert angle(Xg[:, 0], Xo[:, 0]) <= 1e-12
+    assert residual(H, 2.0, Xg[:, 0]) <= 100 * n * EPS
