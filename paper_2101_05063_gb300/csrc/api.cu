@@ -79,6 +79,7 @@ void make_layout(Layout* L, int n, int mr, int mc, int br, int precision) {
     L->off_Ci = take(sizeof(double) * nn * (size_t)(mc > 0 ? mc : 1));
     L->off_S = take(sizeof(double) * nn * m);
     L->off_ZW = take(sizeof(double) * (size_t)br * 2 * L->ncolp);
+    L->off_dt = take(sizeof(double) * N * br * br);
     L->oz = precision == 1 ? 1 : 0;
     {
         const size_t P = L->oz ? hsein::oz_update_hd_elems(*L) : 0;
@@ -152,7 +153,7 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         o.robust = opt->robust;
         if (opt->omega_log2 != 0) o.omega_log2 = opt->omega_log2;
     }
-    if (o.br < 8 || o.br > hsein::kMaxBr) return HSEIN_EARG;
+    if (o.br < 8 || o.br > hsein::kMaxBr || o.br % 8 != 0) return HSEIN_EARG;
     if (o.precision != 0 && o.precision != 1) return HSEIN_EARG;
     if (o.precision == 1 && o.br != 64) return HSEIN_EARG;  // digit tiles are 64 wide
     if (o.robust != 0 && o.robust != 1) return HSEIN_EARG;
@@ -201,6 +202,7 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
     {
         PhaseScope ps(plan, 0, s);
         hsein::launch_prepare(L, dWork, dH, ldh, dWr, dWi, dB, ldb, om, s);
+        hsein::launch_stage_tiles(L, dWork, dH, ldh, s);
         if (L.oz) hsein::launch_split_h(L, dWork, dH, ldh, s);
     }
     for (int J = L.N - 1; J >= 1; --J) {

@@ -16,6 +16,7 @@
 //   double R[ldw*ncolp]           live cross-over columns R~ (one per column)
 //   double Cr[n*m], Ci[n*m], S[n*m]  Givens rotations (Sec. 3.1, eq. givens)
 //   double ZW[br*2*ncolp]         operand [Z'|W] of the shared-H product
+//   double dt[N*br*br]            the diagonal tiles H(J, J^-), staged contiguously
 // split-precision update only (BF16 digits, see ozaki.cuh):
 //   bf16  hd[7 * br * P]          digits of every block H(1:p0(J), J^-), P = sum p0
 //   int   he[P]                   their row exponents
@@ -59,7 +60,7 @@ struct Layout {
     int n, m, mr, mc, ncol, ncolp, br, N, b0, ldw;
     size_t off_state, off_qsrc, off_qcol, off_lam, off_bnorm, off_eB, off_etile, off_bmax,
         off_rmax, off_epi, off_anorm, off_rowpart, off_X, off_R, off_Cr, off_Ci, off_S, off_ZW,
-        off_hd, off_he, off_zwd, off_zwf, off_oz, total;
+        off_dt, off_hd, off_he, off_zwd, off_zwf, off_oz, total;
     int oz;  // 1: split-precision shared-H update (BF16 digits), 0: FP64
 };
 
@@ -106,6 +107,7 @@ void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, i
                  int omega_log2, cudaStream_t s);
 void launch_update(const Layout& L, void* work, const double* H, int ldh, int J, cudaStream_t s);
 void launch_update_oz(const Layout& L, void* work, int J, cudaStream_t s);
+void launch_stage_tiles(const Layout& L, void* work, const double* H, int ldh, cudaStream_t s);
 void launch_split_h(const Layout& L, void* work, const double* H, int ldh, cudaStream_t s);
 size_t oz_update_hd_elems(const Layout& L);
 void launch_finalize(const Layout& L, void* work, double* X, int ldx, int* status,

@@ -1,23 +1,31 @@
 // K1: per-shift work on one diagonal tile J (rows p0 .. p0+bt-1).
 //
-// One warp per shift; lane l owns the tile rows l, l+32, ... .  The H tile
-// H(J, J^-) (columns p0-1 .. p0+bt-2, prescaled) sits in shared memory and is
-// shared by the warps (shifts) of the block.
+// Layout: a group of LPS lanes serves one shift and owns the tile rows
+// r, r+LPS, r+2 LPS, ... (r = lane % LPS); a warp holds 32/LPS shifts.  GB300
+// issues FP64 work per warp instruction whatever the number of active lanes,
+// so the per-step rotation serves every shift of the warp at once, the
+// update loop only runs the row slots that still hold rows above the pivot,
+// and all overflow bookkeeping runs on integer exponents.  The
+// diagonal tile (staged once per solve, contiguous and prescaled) arrives in
+// shared memory with one bulk asynchronous copy completed on an mbarrier.
 //
 // Phase 1 (Alg. "tiled-reduction1" fused with Alg. "solve", i.e. Henry's
 // Alg. "henry" restricted to the tile): for k = bt-1 .. 1 the rotation with
-// [h(k,k-1) v(k)] G^H = [0 phi] is formed (Sec. 3.1 eq. "givens"; complex:
-// eq. "cgivens" with c = v/phi, s = -h/phi), x(k) is divided by phi, column k
-// of R (-s t + conj(c) v, t = h(:,k-1) - lambda e_{k-1}) updates the rows
-// above it, and the working column becomes c t + s v.  Row 0 is closed by the
-// rotation against h(p0, p0-1) (the left cross-over, Alg. "solve") or, on the
+// [h(k,k-1) v(k)] G^H = [0 phi] is formed (eq. "givens"; complex: eq.
+// "cgivens" with c = v/phi, s = -h/phi, phi = sqrt(h^2 + |v|^2)), x(k) is
+// divided by phi, column k of R (conj(c) v - s t, t = h(:,k-1) - lambda
+// e_{k-1}) updates the rows above it, and the working column becomes
+// c t + s v.  With a = x(k) conj(c) and b = x(k) s the two updates of a row
+// are x -= a v - b t and v = c t + s v.  Row 0 is closed by the rotation
+// against h(p0, p0-1) (the left cross-over, Alg. "solve") or, on the
 // top-left tile, by the division by v(0) (padding rotation c = 1, s = 0).
 // Robustness (Sec. 4.1, Alg. "robust-solve"): the tile segment carries one
-// exponent e (stored = true * 2^-e); a division that could exceed 2^omega is
-// preceded by a power-of-two rescale (ProtectDivision), and so is an update
-// whose bound |x| + |R(i,k)| |x(k)| could (ProtectUpdate); |R(i,k)| is bounded
-// by ||H'||_inf + |lambda'| because R's rows are rows of H' - lambda' I times
-// a unitary matrix.
+// exponent e (stored = true * 2^-e).  An integer bound 2^bx on |x| is kept;
+// a division whose result could exceed 2^omega is preceded by a
+// power-of-two rescale (ProtectDivision), and so is an update whose bound
+// |x| + |R(i,k)| |x(k)| could (ProtectUpdate); |R(i,k)| <= ||H'||_inf +
+// |lambda'| because R's rows are rows of H' - lambda' I times a unitary
+// matrix.  Only a bound that fails is refined by an exact maximum.
 //
 // Phase 2 (Alg. "tile-update" lines building rho and z, and the weights of
 // Alg. "tiled-reduction2" written as one product): z = G_{p0+bt-1}^H ...
@@ -27,41 +35,41 @@
 // the common exponent of the rows above is chosen (the consistent scaling
 // min(alpha, beta) of Alg. "robust-tile-update" and one ProtectUpdate over
 // all three linear updates of eq. "robust-update"), and [Z'|W] plus the
-// epilogue constants are written for the shared-H product (k_update).
+// epilogue constants are written for the shared-H product.
 #include "common.cuh"
 #include "ozaki.cuh"
 
 namespace hsein {
 namespace {
 
-constexpr int kWarps = 4;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr long long kWaitLimit = 1LL << 26;  // bounded mbarrier wait (iterations)
 
-__device__ inline double warp_max(double v) {
+// floor(log2|v|) + 1 (v < 2^L) from the exponent bits; kNegInfLog for 0
+__device__ inline int lbound(double v) {
+    const int ex = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    if (ex != 0) return ex - 1022;
+    return v == 0.0 ? kNegInfLog : ilogb(v) + 1;
+}
+
+template <int LPS>
+__device__ inline int group_max_int(int v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 1; o < LPS; o <<= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+template <int LPS>
+__device__ inline double group_max(double v) {
+#pragma unroll
+    for (int o = 1; o < LPS; o <<= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
 
-// q >= 0 such that 2^-q * xabs / dabs <= 2^om (dabs > 0); uses exponents only
-__device__ inline int div_scale(double xabs, double dabs, int om) {
-    if (dabs >= 1.0 || xabs == 0.0) return 0;
-    if (xabs <= dabs * ldexp(1.0, om)) return 0;
-    int q = log2_bound(xabs) - ilogb(dabs) - om;
-    return q < 1 ? 1 : q;
-}
-
-// q >= 0 such that 2^-q (xb + rb * xk) <= 2^om, or 0 if already below
-__device__ inline int upd_scale(double xb, double rb, double xk, int om) {
-    double nb = fma(rb, xk, xb);
-    if (nb <= ldexp(1.0, om)) return 0;
-    int lq = max(log2_bound(xb), log2_bound(rb) + log2_bound(xk)) + 1 - om;
-    return lq < 1 ? 1 : lq;
-}
-
-template <int T, bool CPLX>
-__device__ void tile_shift(const Layout& L, void* work, const double* __restrict__ Hs, int J,
-                           int p0, int bt, int q, int robust, int om, double* sm) {
-    const int lane = threadIdx.x & 31;
+// LPS lanes per shift (32 / LPS shifts per warp), RPL rows per lane
+template <int LPS, int RPL, bool CPLX>
+__device__ void tile_group(const Layout& L, void* work, const double* __restrict__ Hs, int J,
+                           int p0, int bt, int q, bool qok, int robust, int om, double* sm) {
+    const int lane = threadIdx.x & 31, r = lane & (LPS - 1), gbase = lane & ~(LPS - 1);
     const int br = L.br;
     const DevState* st = ws<DevState>(work, L.off_state);
     const double* lamv = ws<double>(work, L.off_lam);
@@ -78,7 +86,7 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
     double* Sv = ws<double>(work, L.off_S);
     double* ZW = ws<double>(work, L.off_ZW);
 
-    // per-warp shared scratch: c (re, im), s, x (re, im), Z' (re, im), W (re, im)
+    // per-group shared scratch: c (re, im), s, x (re, im)
     double* s_cr = sm;
     double* s_ci = sm + br;
     double* s_s = sm + 2 * br;
@@ -87,118 +95,145 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
 
     const double hscale = st->hscale;
     const double hnorm = st->hnorm;
-    const double lre = lamv[2 * q], lim = CPLX ? lamv[2 * q + 1] : 0.0;
-    const int col = qcolumn(L, q);
-    const double Omega = ldexp(1.0, om);
-    const double Rb = hnorm + fabs(lre) + fabs(lim);  // bound on |R(i,k)|
+    const double lre = qok ? lamv[2 * q] : 0.0;
+    const double lim = (CPLX && qok) ? lamv[2 * q + 1] : 0.0;
+    const int col = qok ? qcolumn(L, q) : 0;
+    const int LRb = lbound(hnorm + fabs(lre) + fabs(lim));  // |R(i,k)| < 2^LRb
+    const int cadd = CPLX ? 1 : 0;                            // |z| <= |re| + |im|
+    // integer bound of a (complex) value's magnitude
+    auto lb2 = [&](double a, double b) { return CPLX ? max(lbound(a), lbound(b)) + 1 : lbound(a); };
 
-    double vr[T], vi[T], xr[T], xi[T];
+    double vr[RPL], vi[RPL], xr[RPL], xi[RPL];
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-        int i = lane + 32 * t;
-        bool ok = i < bt;
+    for (int t = 0; t < RPL; ++t) {
+        const int i = r + LPS * t;
+        const bool ok = qok && i < bt;
         vr[t] = ok ? R[p0 + i + (size_t)col * L.ldw] : 0.0;
         xr[t] = ok ? X[p0 + i + (size_t)col * L.ldw] : 0.0;
-        if (CPLX) {
-            vi[t] = ok ? R[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
-            xi[t] = ok ? X[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
-        } else {
-            vi[t] = 0.0;
-            xi[t] = 0.0;
-        }
+        vi[t] = (CPLX && ok) ? R[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
+        xi[t] = (CPLX && ok) ? X[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
     }
-    const int eB0 = eB[q];
+    const int eB0 = qok ? eB[q] : 0;
     int e = eB0;
-    double xbound = 0.0;
+    auto xmax_bound = [&]() {
+        int b = kNegInfLog;
 #pragma unroll
-    for (int t = 0; t < T; ++t) xbound = fmax(xbound, fabs(xr[t]) + fabs(xi[t]));
-    xbound = warp_max(xbound);
-
+        for (int t = 0; t < RPL; ++t) b = max(b, lb2(xr[t], xi[t]));
+        return group_max_int<LPS>(b);
+    };
+    int bx = xmax_bound();
     auto rescale = [&](int sq, double& ar, double& ai) {
 #pragma unroll
-        for (int t = 0; t < T; ++t) {
+        for (int t = 0; t < RPL; ++t) {
             xr[t] = scalbn(xr[t], -sq);
             if (CPLX) xi[t] = scalbn(xi[t], -sq);
         }
         ar = scalbn(ar, -sq);
         if (CPLX) ai = scalbn(ai, -sq);
-        xbound = scalbn(xbound, -sq);
+        bx -= sq;
         e += sq;
     };
 
     // ---------------- phase 1: sweep k = bt-1 .. 1 -----------------------
 #pragma unroll
-    for (int sl = T - 1; sl >= 0; --sl) {
-        for (int kk = 31; kk >= 0; --kk) {
-            const int k = sl * 32 + kk;
+    for (int tk = RPL - 1; tk >= 0; --tk) {
+        for (int rk = LPS - 1; rk >= 0; --rk) {
+            const int k = LPS * tk + rk;
             if (k >= bt || k == 0) continue;
-            double vkr = __shfl_sync(0xffffffffu, vr[sl], kk);
-            double xkr = __shfl_sync(0xffffffffu, xr[sl], kk);
+            const int src = gbase | rk;
+            double vkr = __shfl_sync(kFull, vr[tk], src);
+            double xkr = __shfl_sync(kFull, xr[tk], src);
             double vki = 0.0, xki = 0.0;
             if (CPLX) {
-                vki = __shfl_sync(0xffffffffu, vi[sl], kk);
-                xki = __shfl_sync(0xffffffffu, xi[sl], kk);
+                vki = __shfl_sync(kFull, vi[tk], src);
+                xki = __shfl_sync(kFull, xi[tk], src);
             }
-            const double h = Hs[k * br + k];  // h(p0+k, p0+k-1)
-            double rinv = CPLX ? rhypot(h, hypot(vkr, vki)) : rhypot(h, vkr);
-            const double cr = vkr * rinv, ci = vki * rinv, s = -h * rinv;
-            if (robust) {
-                double xa = fabs(xkr) + fabs(xki);
-                if (rinv > 1.0) {
-                    int sq = div_scale(xa, 1.0 / rinv, om);
-                    if (sq) rescale(sq, xkr, xki);
-                }
+            // rotation: 1/phi = rsqrt(h^2 + |v|^2), guarded against overflow
+            double hs = Hs[k * br + k], vsr = vkr, vsi = vki, sc = 1.0;
+            int eh = max(lbound(hs), lbound(vsr));
+            if (CPLX) eh = max(eh, lbound(vsi));
+            if (eh > 500 || eh < -500) {
+                sc = scalbn(1.0, -eh);
+                hs *= sc;
+                vsr *= sc;
+                if (CPLX) vsi *= sc;
+            }
+            const double ss = CPLX ? fma(vsr, vsr, fma(vsi, vsi, hs * hs)) : fma(vsr, vsr, hs * hs);
+            const double rr = rsqrt(ss);
+            const double cr = vsr * rr, s = -hs * rr;
+            const double ci = CPLX ? vsi * rr : 0.0;
+            const double rinv = rr * sc;
+            if (robust) {  // ProtectDivision: |x(k)| / phi < 2^om
+                const int sq = lb2(xkr, xki) + lbound(rinv) - om;
+                if (sq > 0) rescale(sq, xkr, xki);
             }
             xkr *= rinv;
-            xki *= rinv;
-            if (robust) {
-                double xa = fabs(xkr) + fabs(xki);
-                if (!(fma(Rb, xa, xbound) <= Omega)) {
-                    double ex = 0.0;
-#pragma unroll
-                    for (int t = 0; t < T; ++t) ex = fmax(ex, fabs(xr[t]) + fabs(xi[t]));
-                    xbound = fmax(warp_max(ex), xa);
-                    int sq = upd_scale(xbound, Rb, xa, om);
-                    if (sq) {
-                        rescale(sq, xkr, xki);
-                        xa = fabs(xkr) + fabs(xki);
+            if (CPLX) xki *= rinv;
+            if (robust) {  // ProtectUpdate: |x| + |R| |x(k)| < 2^om
+                const int lx = lb2(xkr, xki);
+                int nb = max(bx, LRb + lx) + 1;
+                const bool refine = nb > om;
+                // the exact maximum is a shuffle over the group: every lane of
+                // the warp takes part whenever any group needs it
+                if (__any_sync(kFull, refine)) {
+                    const int bexact = xmax_bound();
+                    if (refine) {
+                        bx = max(bexact, lx);
+                        nb = max(bx, LRb + lx) + 1;
+                        if (nb > om) {
+                            rescale(nb - om, xkr, xki);
+                            nb = om;
+                        }
                     }
                 }
-                xbound = fma(Rb, xa, xbound);
+                bx = nb;
             }
-            // rows i < k: R(i,k) = -s t + conj(c) v ; x -= R x(k) ; v = c t + s v
+            // a = x(k) conj(c), b = x(k) s
+            const double ar = CPLX ? fma(xkr, cr, xki * ci) : xkr * cr;
+            const double ai = CPLX ? fma(xki, cr, -xkr * ci) : 0.0;
+            const double bR = xkr * s;
+            const double bI = CPLX ? xki * s : 0.0;
 #pragma unroll
-            for (int t = 0; t <= sl; ++t) {
-                const int i = lane + 32 * t;
-                if (t < sl || lane < kk) {
-                    double tr = Hs[k * br + i] - (i == k - 1 ? lre : 0.0);
-                    double ti = (CPLX && i == k - 1) ? -lim : 0.0;
+            for (int t = 0; t <= tk; ++t) {
+                if (t < tk || r < rk) {
+                    const double tr = Hs[k * br + r + LPS * t];
                     if (CPLX) {
-                        // conj(c) v = (cr v_r + ci v_i) + i (cr v_i - ci v_r)
-                        double rr = fma(cr, vr[t], fma(ci, vi[t], -s * tr));
-                        double ri = fma(cr, vi[t], fma(-ci, vr[t], -s * ti));
-                        // x -= R * xk (complex)
-                        xr[t] = fma(-rr, xkr, fma(ri, xki, xr[t]));
-                        xi[t] = fma(-rr, xki, fma(-ri, xkr, xi[t]));
-                        // v = c t + s v
-                        double nvr = fma(cr, tr, fma(-ci, ti, s * vr[t]));
-                        double nvi = fma(cr, ti, fma(ci, tr, s * vi[t]));
+                        // x -= a v - b t
+                        xr[t] = fma(-ar, vr[t], fma(ai, vi[t], fma(bR, tr, xr[t])));
+                        xi[t] = fma(-ar, vi[t], fma(-ai, vr[t], fma(bI, tr, xi[t])));
+                        const double nvr = fma(cr, tr, s * vr[t]);
+                        const double nvi = fma(ci, tr, s * vi[t]);
                         vr[t] = nvr;
                         vi[t] = nvi;
                     } else {
-                        double rr = fma(cr, vr[t], -s * tr);
-                        xr[t] = fma(-rr, xkr, xr[t]);
+                        xr[t] = fma(-ar, vr[t], fma(bR, tr, xr[t]));
                         vr[t] = fma(cr, tr, s * vr[t]);
                     }
                 }
             }
-            if (lane == kk) {
-                xr[sl] = xkr;
-                if (CPLX) xi[sl] = xki;
+            // the shift on the diagonal entry of column k-1 (row k-1):
+            // x -= b lambda, v -= c lambda
+            auto diag_fix = [&](double& xa, double& xb, double& va, double& vb) {
+                if (CPLX) {
+                    xa = fma(-bR, lre, fma(bI, lim, xa));
+                    xb = fma(-bR, lim, fma(-bI, lre, xb));
+                    va = fma(-cr, lre, fma(ci, lim, va));
+                    vb = fma(-cr, lim, fma(-ci, lre, vb));
+                } else {
+                    xa = fma(-bR, lre, xa);
+                    va = fma(-cr, lre, va);
+                }
+            };
+            if (rk > 0) {
+                if (r == rk - 1) diag_fix(xr[tk], xi[tk], vr[tk], vi[tk]);
+            } else if (tk > 0) {
+                if (r == LPS - 1) diag_fix(xr[tk - 1], xi[tk - 1], vr[tk - 1], vi[tk - 1]);
             }
-            if (lane == 0) {
+            if (r == rk) {
+                xr[tk] = xkr;
+                if (CPLX) xi[tk] = xki;
                 s_cr[k] = cr;
-                s_ci[k] = ci;
+                if (CPLX) s_ci[k] = ci;
                 s_s[k] = s;
             }
         }
@@ -206,20 +241,30 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
 
     // ---------------- row 0: left rotation or final pivot ----------------
     {
-        double v0r = __shfl_sync(0xffffffffu, vr[0], 0);
-        double v0i = CPLX ? __shfl_sync(0xffffffffu, vi[0], 0) : 0.0;
-        double x0r = __shfl_sync(0xffffffffu, xr[0], 0);
-        double x0i = CPLX ? __shfl_sync(0xffffffffu, xi[0], 0) : 0.0;
+        double v0r = __shfl_sync(kFull, vr[0], gbase);
+        double v0i = CPLX ? __shfl_sync(kFull, vi[0], gbase) : 0.0;
+        double x0r = __shfl_sync(kFull, xr[0], gbase);
+        double x0i = CPLX ? __shfl_sync(kFull, xi[0], gbase) : 0.0;
         double c0r, c0i, s0;
         if (p0 > 0) {
-            const double h = Hs[0];  // h(p0, p0-1)
-            double rinv = CPLX ? rhypot(h, hypot(v0r, v0i)) : rhypot(h, v0r);
-            c0r = v0r * rinv;
-            c0i = v0i * rinv;
-            s0 = -h * rinv;
-            if (robust && rinv > 1.0) {
-                int sq = div_scale(fabs(x0r) + fabs(x0i), 1.0 / rinv, om);
-                if (sq) rescale(sq, x0r, x0i);
+            double hs = Hs[0], vsr = v0r, vsi = v0i, sc = 1.0;  // h(p0, p0-1)
+            int eh = max(lbound(hs), lbound(vsr));
+            if (CPLX) eh = max(eh, lbound(vsi));
+            if (eh > 500 || eh < -500) {
+                sc = scalbn(1.0, -eh);
+                hs *= sc;
+                vsr *= sc;
+                vsi *= sc;
+            }
+            const double ss = CPLX ? fma(vsr, vsr, fma(vsi, vsi, hs * hs)) : fma(vsr, vsr, hs * hs);
+            const double rr = rsqrt(ss);
+            c0r = vsr * rr;
+            c0i = CPLX ? vsi * rr : 0.0;
+            s0 = -hs * rr;
+            const double rinv = rr * sc;
+            if (robust) {
+                const int sq = lb2(x0r, x0i) + lbound(rinv) - om;
+                if (sq > 0) rescale(sq, x0r, x0i);
             }
             x0r *= rinv;
             x0i *= rinv;
@@ -243,20 +288,20 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
                 pa = small;
             }
             if (robust) {
-                int sq = div_scale(fabs(x0r) + fabs(x0i), pa, om);
-                if (sq) rescale(sq, x0r, x0i);
+                const int sq = lb2(x0r, x0i) - (lbound(pa) - 1) - om;
+                if (sq > 0) rescale(sq, x0r, x0i);
             }
             if (CPLX) {
                 // Smith's division (x0r + i x0i) / (pr + i pi)
                 double nr, ni;
                 if (fabs(pr) >= fabs(pi)) {
-                    double r = pi / pr, d = pr + pi * r;
-                    nr = (x0r + x0i * r) / d;
-                    ni = (x0i - x0r * r) / d;
+                    double rt = pi / pr, d = pr + pi * rt;
+                    nr = (x0r + x0i * rt) / d;
+                    ni = (x0i - x0r * rt) / d;
                 } else {
-                    double r = pr / pi, d = pi + pr * r;
-                    nr = (x0r * r + x0i) / d;
-                    ni = (x0i * r - x0r) / d;
+                    double rt = pr / pi, d = pi + pr * rt;
+                    nr = (x0r * rt + x0i) / d;
+                    ni = (x0i * rt - x0r) / d;
                 }
                 x0r = nr;
                 x0i = ni;
@@ -264,7 +309,7 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
                 x0r /= pr;
             }
         }
-        if (lane == 0) {
+        if (r == 0) {
             xr[0] = x0r;
             if (CPLX) xi[0] = x0i;
             s_cr[0] = c0r;
@@ -272,118 +317,164 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
             s_s[0] = s0;
         }
     }
-    __syncwarp();
 
     // ---------------- outputs of phase 1 ---------------------------------
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-        int i = lane + 32 * t;
+    for (int t = 0; t < RPL; ++t) {
+        const int i = r + LPS * t;
         if (i < bt) {
-            X[p0 + i + (size_t)col * L.ldw] = xr[t];
             s_xr[i] = xr[t];
-            if (CPLX) {
-                X[p0 + i + (size_t)(col + 1) * L.ldw] = xi[t];
-                s_xi[i] = xi[t];
+            if (CPLX) s_xi[i] = xi[t];
+            if (qok) {
+                X[p0 + i + (size_t)col * L.ldw] = xr[t];
+                if (CPLX) X[p0 + i + (size_t)(col + 1) * L.ldw] = xi[t];
             }
         }
     }
-    for (int i = lane; i < bt; i += 32) {
-        size_t g = (size_t)q * L.n + p0 + i;
-        Cr[g] = s_cr[i];
-        Sv[g] = s_s[i];
-        if (CPLX) Ci[g] = s_ci[i];
+    __syncwarp();
+    if (qok) {
+        for (int i = r; i < bt; i += LPS) {
+            const size_t gi = (size_t)q * L.n + p0 + i;
+            Cr[gi] = s_cr[i];
+            Sv[gi] = s_s[i];
+            if (CPLX) Ci[gi] = s_ci[i];
+        }
+        if (r == 0) etile[(size_t)J * L.m + q] = e;
     }
-    if (lane == 0) etile[(size_t)J * L.m + q] = e;
     __syncwarp();
     if (p0 == 0) return;
 
-    // ---------------- phase 2: [Z'|W], scale exponent, epilogue ----------
+    // ---------------- phase 2: [Z'|W] by a parallel scan ------------------
+    // tau_k = s_k tau_{k-1} + conj(c_k) x_k (tau_0 = conj(c_0) x_0) is an
+    // affine recurrence and P_k = prod_{i<=k} s_i a product recurrence: each
+    // lane composes the maps of a contiguous chunk of rows, the group scans
+    // the chunks, then each lane emits Z'(k) = c_k tau_{k-1} - s_k x_k
+    // (Z'(0) = rho' = -s_0 x_0) and w_k = c_k P_{k-1} (w_0 = c_0) for its rows.
     double* s_zr = s_xr;  // Z' and W overwrite the x and c scratch in place
     double* s_zi = s_xi;
-    if (lane == 0) {
-        // z = G^H [0; x]: rho' = -s_0 x_0, tau = conj(c_0) x_0, then
-        // (Z'(k), tau) = (c_k tau - s_k x_k, s_k tau + conj(c_k) x_k)
-        double c0r = s_cr[0], c0i = s_ci[0], s0 = s_s[0];
-        double x0r = s_xr[0], x0i = CPLX ? s_xi[0] : 0.0;
-        double tr = c0r * x0r + c0i * x0i;
-        double ti = CPLX ? (c0r * x0i - c0i * x0r) : 0.0;
-        double rhor = -s0 * x0r, rhoi = -s0 * x0i;
-        s_zr[0] = rhor;
-        if (CPLX) s_zi[0] = rhoi;
-        double zmax = CPLX ? hypot(rhor, rhoi) : fabs(rhor);
-        // W (prefix products) is written into the cosine scratch in place
-        double pr = s0;  // prod of s_i for i < k
-        // w_0 = c_0 stays in s_cr[0], s_ci[0]
-        for (int k = 1; k < bt; ++k) {
-            double ckr = s_cr[k], cki = s_ci[k], sk = s_s[k];
-            double xkr = s_xr[k], xki = CPLX ? s_xi[k] : 0.0;
-            double zr = ckr * tr - cki * ti - sk * xkr;
-            double zi = CPLX ? (ckr * ti + cki * tr - sk * xki) : 0.0;
-            // tau <- s tau + conj(c) x
-            double ntr = sk * tr + ckr * xkr + cki * xki;
-            double nti = CPLX ? (sk * ti + ckr * xki - cki * xkr) : 0.0;
+    const int cs = (bt + LPS - 1) / LPS;
+    const int a0 = min(bt, r * cs), a1 = min(bt, a0 + cs);
+    double mA = 1.0, mBr = 0.0, mBi = 0.0, mP = 1.0;
+    for (int k = a0; k < a1; ++k) {
+        const double ckr = s_cr[k], sk = s_s[k], xkr = s_xr[k];
+        const double cki = CPLX ? s_ci[k] : 0.0, xki = CPLX ? s_xi[k] : 0.0;
+        const double gr = CPLX ? fma(ckr, xkr, cki * xki) : ckr * xkr;
+        const double gi = CPLX ? fma(ckr, xki, -cki * xkr) : 0.0;
+        const double a = k == 0 ? 0.0 : sk;
+        mA *= a;
+        mBr = fma(a, mBr, gr);
+        if (CPLX) mBi = fma(a, mBi, gi);
+        mP *= sk;
+    }
+    // inclusive scan over the group (earlier chunks applied first)
+#pragma unroll
+    for (int o = 1; o < LPS; o <<= 1) {
+        const double pA = __shfl_up_sync(kFull, mA, o, LPS);
+        const double pBr = __shfl_up_sync(kFull, mBr, o, LPS);
+        const double pBi = CPLX ? __shfl_up_sync(kFull, mBi, o, LPS) : 0.0;
+        const double pP = __shfl_up_sync(kFull, mP, o, LPS);
+        if (r >= o) {
+            mBr = fma(mA, pBr, mBr);
+            if (CPLX) mBi = fma(mA, pBi, mBi);
+            mA *= pA;
+            mP *= pP;
+        }
+    }
+    double tr = __shfl_up_sync(kFull, mBr, 1, LPS);  // tau entering the chunk
+    double ti = CPLX ? __shfl_up_sync(kFull, mBi, 1, LPS) : 0.0;
+    double P = __shfl_up_sync(kFull, mP, 1, LPS);     // prod of s_i before the chunk
+    if (r == 0) {
+        tr = 0.0;
+        ti = 0.0;
+        P = 1.0;
+    }
+    double zmax = 0.0;
+    for (int k = a0; k < a1; ++k) {
+        const double ckr = s_cr[k], sk = s_s[k], xkr = s_xr[k];
+        const double cki = CPLX ? s_ci[k] : 0.0, xki = CPLX ? s_xi[k] : 0.0;
+        double zr, zi;
+        if (k == 0) {
+            zr = -sk * xkr;
+            zi = CPLX ? -sk * xki : 0.0;
+            tr = CPLX ? fma(ckr, xkr, cki * xki) : ckr * xkr;
+            ti = CPLX ? fma(ckr, xki, -cki * xkr) : 0.0;
+        } else {
+            zr = CPLX ? fma(ckr, tr, fma(-cki, ti, -sk * xkr)) : fma(ckr, tr, -sk * xkr);
+            zi = CPLX ? fma(ckr, ti, fma(cki, tr, -sk * xki)) : 0.0;
+            const double ntr = CPLX ? fma(sk, tr, fma(ckr, xkr, cki * xki)) : fma(sk, tr, ckr * xkr);
+            const double nti = CPLX ? fma(sk, ti, fma(ckr, xki, -cki * xkr)) : 0.0;
             tr = ntr;
             ti = nti;
-            s_zr[k] = zr;
-            if (CPLX) s_zi[k] = zi;
-            zmax = fmax(zmax, CPLX ? hypot(zr, zi) : fabs(zr));
-            s_cr[k] = ckr * pr;  // w_k = c_k prod_{i<k} s_i
-            s_ci[k] = cki * pr;
-            pr *= sk;
         }
-        const double pi_ = pr;
-        const double zbr_r = tr, zbr_i = ti;
-
+        s_zr[k] = zr;
+        if (CPLX) s_zi[k] = zi;
+        zmax = fmax(zmax, CPLX ? fmax(fabs(zr), fabs(zi)) : fabs(zr));
+        s_cr[k] = ckr * P;  // w_k = c_k prod_{i<k} s_i (w_0 = c_0)
+        if (CPLX) s_ci[k] = cki * P;
+        P *= sk;
+    }
+    zmax = group_max<LPS>(zmax);
+    const int last = gbase + (bt - 1) / cs;
+    const double zbr_r = __shfl_sync(kFull, tr, last);
+    const double zbr_i = CPLX ? __shfl_sync(kFull, ti, last) : 0.0;
+    const double pi_ = __shfl_sync(kFull, P, last);
+    __syncwarp();
+    if (r == 0) {
+        const double rhor = s_zr[0], rhoi = CPLX ? s_zi[0] : 0.0;
         // consistent exponent for the rows above (Alg. "robust-tile-update"):
         // B_new = B 2^(eB-e) - (A Z' + R~ z_br - lambda rho' e_last) 2^(ex-e)
         const int ex = e;
         int enew = max(eB0, ex);
-        if (robust) {
-            const int cadd = CPLX ? 1 : 0;
+        if (robust && qok) {
             const double An = bits_to_double(anorm[J]) * hscale;
             const double bm = bits_to_double(bmaxv[q]);
             const double rm = bits_to_double(rmaxv[q]);
-            const double la = CPLX ? hypot(lre, lim) : fabs(lre);
-            const double rh = CPLX ? hypot(rhor, rhoi) : fabs(rhor);
-            const double zb = CPLX ? hypot(zbr_r, zbr_i) : fabs(zbr_r);
-            int lt = max(log2_bound(An) + log2_bound(zmax),
-                         max(log2_bound(rm) + cadd + log2_bound(zb), log2_bound(la) + log2_bound(rh))) + 2;
-            int lb = log2_bound(bm) + cadd;
-            int need = max(lb + eB0, lt + ex) + 1 - om;
+            const double la = fabs(lre) + fabs(lim);
+            const double rh = fabs(rhor) + fabs(rhoi);
+            const double zb = fabs(zbr_r) + fabs(zbr_i);
+            const int lt = max(log2_bound(An) + log2_bound(zmax) + cadd,
+                               max(log2_bound(rm) + cadd + log2_bound(zb),
+                                   log2_bound(la) + log2_bound(rh))) + 2;
+            const int lbm = log2_bound(bm) + cadd;
+            const int need = max(lbm + eB0, lt + ex) + 1 - om;
             enew = max(enew, need);
         }
         const double fB = ldexp(1.0, eB0 - enew);
         const double fZ = ldexp(1.0, ex - enew);
-        eB[q] = enew;
-        bmaxv[q] = 0ull;
-        rmaxv[q] = 0ull;
-        Epi E;
-        E.fB = fB;
-        E.pi = pi_;
-        E.zbr_re = zbr_r * fZ;
-        E.zbr_im = zbr_i * fZ;
-        // lambda' rho' fZ and lambda' c_0
-        E.cz_re = (lre * rhor - lim * rhoi) * fZ;
-        E.cz_im = (lre * rhoi + lim * rhor) * fZ;
-        E.cw_re = lre * s_cr[0] - lim * s_ci[0];
-        E.cw_im = lre * s_ci[0] + lim * s_cr[0];
-        epi[q] = E;
+        if (qok) {
+            eB[q] = enew;
+            bmaxv[q] = 0ull;
+            rmaxv[q] = 0ull;
+            Epi E;
+            E.fB = fB;
+            E.pi = pi_;
+            E.zbr_re = zbr_r * fZ;
+            E.zbr_im = zbr_i * fZ;
+            // lambda' rho' fZ and lambda' c_0 (s_cr[0] = w_0 = c_0)
+            E.cz_re = (lre * rhor - lim * rhoi) * fZ;
+            E.cz_im = (lre * rhoi + lim * rhor) * fZ;
+            E.cw_re = lre * s_cr[0] - lim * s_ci[0];
+            E.cw_im = lre * s_ci[0] + lim * s_cr[0];
+            epi[q] = E;
+        }
         s_s[0] = fZ * hscale;  // reuse: factor for Z'
     }
     __syncwarp();
     const double fz = s_s[0];
     const size_t ldzw = 2 * (size_t)L.ncolp;
     if (!L.oz) {
-        for (int k = lane; k < bt; k += 32) {
-            double* row = ZW + (size_t)k * ldzw + 2 * (size_t)col;
-            if (CPLX) {
-                row[0] = s_zr[k] * fz;
-                row[1] = s_cr[k] * hscale;
-                row[2] = s_zi[k] * fz;
-                row[3] = s_ci[k] * hscale;
-            } else {
-                row[0] = s_zr[k] * fz;
-                row[1] = s_cr[k] * hscale;
+        if (qok) {
+            for (int k = r; k < bt; k += LPS) {
+                double* row = ZW + (size_t)k * ldzw + 2 * (size_t)col;
+                if (CPLX) {
+                    row[0] = s_zr[k] * fz;
+                    row[1] = s_cr[k] * hscale;
+                    row[2] = s_zi[k] * fz;
+                    row[3] = s_ci[k] * hscale;
+                } else {
+                    row[0] = s_zr[k] * fz;
+                    row[1] = s_cr[k] * hscale;
+                }
             }
         }
     } else {
@@ -392,80 +483,164 @@ __device__ void tile_shift(const Layout& L, void* work, const double* __restrict
         int* zf = ws<int>(work, L.off_zwf);
         const int ncols = CPLX ? 4 : 2;
         for (int cc = 0; cc < ncols; ++cc) {
-            const double* src = (cc & 1) ? ((cc & 2) ? s_ci : s_cr) : ((cc & 2) ? s_zi : s_zr);
+            const double* srcv = (cc & 1) ? ((cc & 2) ? s_ci : s_cr) : ((cc & 2) ? s_zi : s_zr);
             const double f = (cc & 1) ? hscale : fz;
-            double v0 = lane < bt ? src[lane] * f : 0.0;
-            double v1 = lane + 32 < bt ? src[lane + 32] * f : 0.0;
-            double m = warp_max(fmax(fabs(v0), fabs(v1)));
-            const int e = oz::scale_exponent(m);
+            double m = 0.0;
+            for (int k = r; k < bt; k += LPS) m = fmax(m, fabs(srcv[k] * f));
+            m = group_max<LPS>(m);  // every lane takes part (shuffle)
+            if (!qok) continue;
+            const int es = oz::scale_exponent(m);
             const int gc = 2 * col + cc;
-            if (lane == 0) zf[gc] = e;
+            if (r == 0) zf[gc] = es;
+            for (int k = r; k < br; k += LPS) {
+                int d[oz::kS];
+                oz::split_digits(k < bt ? srcv[k] * f : 0.0, es, d);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = lane + 32 * h;
-                if (k < br) {
-                    int d[oz::kS];
-                    oz::split_digits(h ? v1 : v0, e, d);
-#pragma unroll
-                    for (int i = 0; i < oz::kS; ++i)
-                        zd[((size_t)i * ldzw + gc) * br + k] = __float2bfloat16_rn((float)d[i]);
-                }
+                for (int i = 0; i < oz::kS; ++i)
+                    zd[((size_t)i * ldzw + gc) * br + k] = __float2bfloat16_rn((float)d[i]);
             }
         }
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(kWarps * 32)
-k_diag(Layout L, void* work, const double* __restrict__ H, int ldh, int J, int robust, int om) {
-    extern __shared__ __align__(16) double smem[];
-    const DevState* st = ws<DevState>(work, L.off_state);
+__device__ inline uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+template <int LPSC, int RPLC, int LPSR, int RPLR>
+__global__ void __launch_bounds__(32)
+k_diag(Layout L, void* work, int J, int robust, int om, int nbc) {
+    extern __shared__ __align__(128) double smem[];
+    __shared__ __align__(8) unsigned long long mbar;
+    DevState* st = ws<DevState>(work, L.off_state);
     if (st->status < 0) return;
     const int br = L.br;
-    double* Hs = smem;  // [br cols][br rows]
-    double* scratch = smem + (size_t)br * br + (size_t)(threadIdx.x >> 5) * 5 * br;
+    const int lane = threadIdx.x;
     const int p0 = tile_start(L, J);
     const int bt = tile_height(L, J);
-    const double hscale = st->hscale;
-    for (int idx = threadIdx.x; idx < bt * bt; idx += blockDim.x) {
-        int cc = idx / bt, i = idx % bt;
-        int gc = p0 - 1 + cc;
-        double v = 0.0;
-        if (gc >= 0 && i <= cc) v = H[p0 + i + (size_t)gc * ldh] * hscale;
-        Hs[cc * br + i] = v;
+    double* Hs = smem;  // [br cols][br rows], column cc = global column p0-1+cc
+    // one bulk copy of the staged (contiguous, prescaled) tile
+    const double* tile = ws<double>(work, L.off_dt) + (size_t)J * br * br;
+    const uint32_t bytes = (uint32_t)((size_t)bt * br * sizeof(double));
+    const uint32_t mb = smem_u32(&mbar);
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
-    __syncthreads();
-    const int q = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (q >= L.m) return;
-    if (q < L.mc)
-        tile_shift<T, true>(L, work, Hs, J, p0, bt, q, robust, om, scratch);
-    else
-        tile_shift<T, false>(L, work, Hs, J, p0, bt, q, robust, om, scratch);
+    __syncwarp();
+    if (lane == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes));
+        asm volatile(
+            "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_u32(Hs)),
+            "l"(tile), "r"(bytes), "r"(mb)
+            : "memory");
+    }
+    long long spins = 0;
+    uint32_t done = 0;
+    while (true) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mb)
+            : "memory");
+        if (done) break;
+        if (++spins > kWaitLimit) {  // the copy never completed: report and stop
+            if (lane == 0) set_error(st, -5);
+            return;
+        }
+    }
+    const int b = blockIdx.x;
+    if (b < nbc) {
+        constexpr int G = 32 / LPSC;
+        const int g = lane / LPSC;
+        const int q = G * b + g;
+        double* scratch = smem + (size_t)br * br + (size_t)g * 5 * br;
+        tile_group<LPSC, RPLC, true>(L, work, Hs, J, p0, bt, q, q < L.mc, robust, om, scratch);
+    } else {
+        constexpr int G = 32 / LPSR;
+        const int g = lane / LPSR;
+        const int q = L.mc + G * (b - nbc) + g;
+        double* scratch = smem + (size_t)br * br + (size_t)g * 5 * br;
+        tile_group<LPSR, RPLR, false>(L, work, Hs, J, p0, bt, q, q < L.m, robust, om, scratch);
+    }
+}
+
+// stage every diagonal tile H(J, J^-) once per solve: contiguous, column
+// cc = global column p0-1+cc, prescaled, zero below the subdiagonal (those
+// entries of H are not read)
+__global__ void k_stage_tiles(Layout L, void* work, const double* __restrict__ H, int ldh) {
+    const DevState* st = ws<DevState>(work, L.off_state);
+    if (st->status < 0) return;
+    const int J = blockIdx.x;
+    const int br = L.br;
+    const int p0 = tile_start(L, J), bt = tile_height(L, J);
+    const double hscale = st->hscale;
+    double* dt = ws<double>(work, L.off_dt) + (size_t)J * br * br;
+    for (int idx = threadIdx.x; idx < bt * br; idx += blockDim.x) {
+        const int cc = idx / br, i = idx % br;
+        const int gc = p0 - 1 + cc;
+        double v = 0.0;
+        if (i < bt && gc >= 0 && i <= cc) v = H[p0 + i + (size_t)gc * ldh] * hscale;
+        dt[idx] = v;
+    }
 }
 
 }  // namespace
 
+void launch_stage_tiles(const Layout& L, void* work, const double* H, int ldh, cudaStream_t s) {
+    k_stage_tiles<<<L.N, 256, 0, s>>>(L, work, H, ldh);
+}
+
+// lanes per shift: complex shifts take a whole warp, real shifts half of one
+// (the FP64 unit of an SM sub-partition serves one warp instruction at a time,
+// so fewer shifts per warp spread the sweep over more sub-partitions)
+constexpr int kLpsC = 32, kLpsR = 16;
+constexpr int kMaxGroups = 32 / kLpsR;
+
+static int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <int RC, int RR>
+static void launch_t(const Layout& L, void* work, int J, int robust, int om, int nbc, int grid,
+                     size_t smem, cudaStream_t s) {
+    k_diag<kLpsC, RC, kLpsR, RR><<<grid, 32, smem, s>>>(L, work, J, robust, om, nbc);
+}
+
+static size_t diag_smem(int br) {
+    return ((size_t)br * br + (size_t)kMaxGroups * 5 * br) * sizeof(double);
+}
+
 void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, int robust,
                  int omega_log2, cudaStream_t s) {
-    int grid = (L.m + kWarps - 1) / kWarps;
-    size_t smem = ((size_t)L.br * L.br + (size_t)kWarps * 5 * L.br) * sizeof(double);
-    if (L.br <= 32) {
-        k_diag<1><<<grid, kWarps * 32, smem, s>>>(L, work, H, ldh, J, robust, omega_log2);
-    } else if (L.br <= 64) {
-        k_diag<2><<<grid, kWarps * 32, smem, s>>>(L, work, H, ldh, J, robust, omega_log2);
-    } else {
-        k_diag<4><<<grid, kWarps * 32, smem, s>>>(L, work, H, ldh, J, robust, omega_log2);
+    (void)H;
+    (void)ldh;
+    const int nbc = (L.mc + (32 / kLpsC) - 1) / (32 / kLpsC);
+    const int nbr = (L.mr + (32 / kLpsR) - 1) / (32 / kLpsR);
+    const size_t smem = diag_smem(L.br);
+    const int grid = nbc + nbr;
+    // rows per lane, rounded up to a power of two: complex br/32, real br/16
+    switch (pow2_at_least((L.br + kLpsR - 1) / kLpsR)) {
+        case 1: launch_t<1, 1>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
+        case 2: launch_t<1, 2>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
+        case 4: launch_t<2, 4>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
+        default: launch_t<4, 8>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
     }
 }
 
 // dynamic shared memory above 48 KB needs an opt-in per kernel
 cudaError_t diag_configure(int br) {
-    size_t smem = ((size_t)br * br + (size_t)kWarps * 5 * br) * sizeof(double);
-    cudaError_t e = cudaSuccess;
-    if (br <= 32) e = cudaFuncSetAttribute(k_diag<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else if (br <= 64) e = cudaFuncSetAttribute(k_diag<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else e = cudaFuncSetAttribute(k_diag<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return e;
+    const int smem = (int)diag_smem(br);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    switch (pow2_at_least((br + kLpsR - 1) / kLpsR)) {
+        case 1: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 1>, a, smem);
+        case 2: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 2>, a, smem);
+        case 4: return cudaFuncSetAttribute(k_diag<kLpsC, 2, kLpsR, 4>, a, smem);
+        default: return cudaFuncSetAttribute(k_diag<kLpsC, 4, kLpsR, 8>, a, smem);
+    }
 }
 
 }  // namespace hsein
