@@ -277,62 +277,73 @@ def main():
     n, ncol, m = inst.n, inst.ncol, inst.m
     f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device=dev)
     dH, dwr, dwi, dB, dQ = f(inst.H), f(inst.wr), f(inst.wi), f(inst.B), f(inst.Q0)
-    solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=args.br, device=dev)
     X = torch.empty((ncol, n), dtype=torch.float64, device=dev).t()
     Z = torch.empty((ncol, n), dtype=torch.float64, device=dev).t()
     status = torch.empty(m, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        solver.solve(dH, dwr, dwi, dB, X=X, status=status, check=False)
-        solver.backtransform(dQ, X, Z=Z)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    dstat = solver.device_status()
-    if dstat < 0:
-        raise RuntimeError("device status %d" % dstat)
-    # accuracy of this run: normwise residual of every converged column
-    sh = status.cpu().numpy()
-    HX = (dH @ X).cpu().numpy()
-    Xh = X.cpu().numpy()
     offs = hi.column_offsets(inst.wi)
     hn1 = np.abs(inst.H).sum(axis=0).max()
-    worst = 0.0
-    for l in range(m):
-        if sh[l] != 0:
-            continue
-        c0, c1 = offs[l], offs[l + 1]
-        if c1 - c0 == 2:
-            lam = complex(inst.wr[l], inst.wi[l])
-            x, hx = Xh[:, c0] + 1j * Xh[:, c0 + 1], HX[:, c0] + 1j * HX[:, c0 + 1]
-        else:
-            lam, x, hx = inst.wr[l], Xh[:, c0], HX[:, c0]
-        worst = max(worst, np.abs(hx - lam * x).sum() / (hn1 * np.abs(x).sum()))
 
-    # ---------------- timed region: device-resident inputs ------------------
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    if sampler:
-        sampler.start()
-    hs.hsein_plan_set_profiling(solver.plan, True)
-    hs.hsein_plan_profile(solver.plan, reset=True)
-    barrier(world)
-    torch.cuda.synchronize()
+    def residual_max(sh):
+        """Largest normwise residual over the converged columns (FP64 on the
+        device), in units of n eps."""
+        HX = (dH @ X).cpu().numpy()
+        Xh = X.cpu().numpy()
+        worst = 0.0
+        for l in range(m):
+            if sh[l] != 0:
+                continue
+            c0, c1 = offs[l], offs[l + 1]
+            if c1 - c0 == 2:
+                lam = complex(inst.wr[l], inst.wi[l])
+                x, hx = Xh[:, c0] + 1j * Xh[:, c0 + 1], HX[:, c0] + 1j * HX[:, c0 + 1]
+            else:
+                lam, x, hx = inst.wr[l], Xh[:, c0], HX[:, c0]
+            worst = max(worst, np.abs(hx - lam * x).sum() / (hn1 * np.abs(x).sum()))
+        return worst / (n * EPS)
+
+    def measure(precision, sample_clocks):
+        """Warm up, check, then time args.steps steps of one precision mode."""
+        solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=args.br, precision=precision,
+                           device=dev)
+
+        def step():
+            solver.solve(dH, dwr, dwi, dB, X=X, status=status, check=False)
+            solver.backtransform(dQ, X, Z=Z)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        dstat = solver.device_status()
+        if dstat < 0:
+            raise RuntimeError("device status %d" % dstat)
+        sh = status.cpu().numpy()
+        worst = residual_max(sh)
+        sampler = ClockSampler(torch.cuda.current_device()) if (rank == 0 and sample_clocks) else None
+        if sampler:
+            sampler.start()
+        hs.hsein_plan_set_profiling(solver.plan, True)
+        hs.hsein_plan_profile(solver.plan, reset=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        prof = hs.hsein_plan_profile(solver.plan, reset=True)
+        hs.hsein_plan_set_profiling(solver.plan, False)
+        clocks = sampler.stop() if sampler else None
+        return solver, step, max_over_ranks(ms, world), prof, worst, sh, clocks
+
+    solver, step, ms, prof, worst, sh, clocks = measure(0, True)
+    value = world * ncol * args.steps / (ms * 1e-3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    ms = e0.elapsed_time(e1)
-    prof = hs.hsein_plan_profile(solver.plan, reset=True)
-    hs.hsein_plan_set_profiling(solver.plan, False)
-    clocks = sampler.stop() if sampler else None
-    ms = max_over_ranks(ms, world)
-    value = world * ncol * args.steps / (ms * 1e-3)
 
     # ---------------- end to end through the API with host buffers ---------
     pin = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64).pin_memory()
@@ -364,6 +375,11 @@ def main():
     ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = world * ncol * args.steps / (ms_e2e * 1e-3)
 
+    # ---------------- the split-precision path on the same inputs ----------
+    del solver
+    _, _, ms_sp, prof_sp, worst_sp, sh_sp, _ = measure(1, False)
+    value_sp = world * ncol * args.steps / (ms_sp * 1e-3)
+
     if rank != 0:
         return
     pk, pk_kind = peaks()
@@ -384,9 +400,29 @@ def main():
         kname = "k_update"
         dominant = "shared_h_update"
     achieved = flops_launch / (t_launch * 1e-3) / 1e12
-    # prepare is four kernels (setup, row sums, tile norms, init); the other
-    # phases are one kernel per recorded launch
-    launches = 4 * prof["prepare"][1] + sum(v[1] for k, v in prof.items() if k != "prepare")
+    # prepare is five kernels (setup, row sums, tile norms, init, tile
+    # staging); the other phases are one kernel per recorded launch
+    launches = 5 * prof["prepare"][1] + sum(v[1] for k, v in prof.items() if k != "prepare")
+    # split mode: the digit products run on the BF16 tensor cores; 28 digit
+    # pairs per product (7 digits, pairs above the FP64 rounding level)
+    t_upd_sp = prof_sp["shared_h_update"][0] / args.steps
+    t_q0_sp = prof_sp["q0_backtransform"][0] / args.steps
+    tensor_upd = 28.0 * uf / (t_upd_sp * 1e-3) / 1e12
+    tensor_q0 = 28.0 * q0f / (t_q0_sp * 1e-3) / 1e12
+    split = {
+        "value": value_sp, "unit": UNIT, "ms_per_step": ms_sp / args.steps,
+        "vs_plain_fp64": value_sp / value,
+        "residual_max_over_n_eps": worst_sp, "not_converged": int((sh_sp != 0).sum()),
+        "phases": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                   for k, v in prof_sp.items()},
+        "tensor": {"peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                   "shared_h_update_achieved": tensor_upd,
+                   "shared_h_update_frac": tensor_upd / pk["bf16_tflops"],
+                   "q0_backtransform_achieved": tensor_q0,
+                   "q0_backtransform_frac": tensor_q0 / pk["bf16_tflops"],
+                   "engine": "mma.sync m16n8k16 bf16 -> fp32"},
+        "dtype": "f64 results; bf16 digit products with exact integer accumulation",
+    }
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -399,12 +435,13 @@ def main():
                                     % (pk_kind, pk["bf16_tflops"]),
                      "algorithmic_flops_per_launch": flops_launch},
         "phases": phases,
-        "residual_max_over_n_eps": worst / (n * EPS),
+        "residual_max_over_n_eps": worst,
         "not_converged": int((sh != 0).sum()),
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "split_precision": split,
     }
     if not args.no_cpu_baseline and world == 1:
         v, cores, desc = cpu_baseline(inst, args.cpu_sample)
