@@ -240,8 +240,11 @@ hsein_status hsein_backtransform(hsein_plan_t plan, const double* dQ0, int ldq, 
         if (!dWork || !aligned256(dWork)) return HSEIN_EARG;
         if (work_bytes < L.total) return HSEIN_ENOMEM;
         PhaseScope ps(plan, 4, s);
-        hsein::launch_ozaki_q0(L.n, L.ncol, dQ0, ldq, dX, ldx, dZ, ldz,
-                               static_cast<char*>(dWork) + L.off_oz, s);
+        int* status_word = reinterpret_cast<int*>(static_cast<char*>(dWork) + L.off_state +
+                                                  offsetof(hsein::DevState, status));
+        if (!hsein::launch_ozaki_q0(L.n, L.ncol, dQ0, ldq, dX, ldx, dZ, ldz,
+                                    static_cast<char*>(dWork) + L.off_oz, status_word, s))
+            return HSEIN_ECUDA;
     } else {
         PhaseScope ps(plan, 4, s);
         hsein::launch_q0(L, dQ0, ldq, dX, ldx, dZ, ldz, s);

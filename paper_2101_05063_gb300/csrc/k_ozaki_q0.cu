@@ -4,22 +4,30 @@
 //   k_oz_rowmax     max |Q0(r,:)| per row (exponent of the row)
 //   k_oz_split_rows Q0 -> kS BF16 digit matrices, k-contiguous rows
 //   k_oz_split_cols X  -> kS BF16 digit matrices per column, with exponents
-//   k_oz_gemm       the 28 digit-pair products (i + j < kS) with mma.sync
-//                   m16n8k16 BF16 -> FP32, exact integer accumulation of the
-//                   leading diagonals, FP64 recombination once per output.
+//   k_oz_gemm       the 28 digit-pair products (i + j < kS) on the 5th-gen
+//                   tensor cores: TMA brings 32-wide K slices of all 7 digit
+//                   matrices of both operands into shared memory (2 stages);
+//                   one thread issues tcgen05.mma BF16 x BF16 -> FP32 into 7
+//                   diagonal accumulators in TMEM (10 MMAs per K-step, each A
+//                   digit against a run of B digits); epilogue warps fold the
+//                   leading diagonals into exact int64 every 256 of K and
+//                   recombine in FP64 once per output.
 #include "common.cuh"
 #include "ozaki.cuh"
+#include "tc.cuh"
 
 namespace hsein {
 namespace {
 
-using oz::kKc;
 using oz::kS;
 
-constexpr int BM = 64, BN = 64, BK = 32, STAGES = 3;
-constexpr int kTileElems = BM * BK;                 // per digit matrix, per operand
-constexpr int kStageBytes = 2 * kS * kTileElems * 2;  // A and B, kS digits, bf16
-constexpr int kSmemBytes = STAGES * kStageBytes;
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2;
+constexpr int kABytes = kS * BM * BK * 2;             // one stage of A digits (7 x 8 KB)
+constexpr int kBBytes = kS * BN * BK * 2;             // one stage of B digits (7 x 4 KB)
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kSmemBytes = STAGES * kStageBytes + 1024;  // + alignment slack
+constexpr int kChunkBlocks = 256 / BK;  // exact FP32 span of diagonals 0..3 (4 x 256 x 2^14 <= 2^24)
+constexpr int kTmemCols = 512;          // 7 diagonals x 64 columns, rounded to a power of two
 
 struct OzLayout {
     int Mp, Np, Kp;
@@ -118,170 +126,199 @@ __global__ void k_oz_split_cols(int K, int N, const double* __restrict__ B, int 
     }
 }
 
-__device__ inline uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+// One K-step of the digit products, as MMAs of A digit i against the B digits
+// j0 .. j0+nj-1.  The B digit matrices sit one after another in shared memory
+// (64 rows each), so they form one operand with N = 64 nj, and its output
+// columns land on the diagonal accumulators i+j0 .. i+j0+nj-1 directly.  The
+// first six pieces touch only diagonals >= kTopDiag; they are issued before
+// the epilogue has released diagonals 0..3 of the previous chunk.
+struct Piece {
+    int i, j0, nj;
+};
+constexpr int kPieces = 10, kLowPieces = 6;
+__constant__ const Piece kPiece[kPieces] = {{0, 4, 3}, {1, 4, 2}, {2, 4, 1}, {4, 0, 3}, {5, 0, 2},
+                                            {6, 0, 1}, {0, 0, 4}, {1, 0, 4}, {2, 0, 4}, {3, 0, 4}};
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, 32 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
-__device__ inline void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
-}
-
-__device__ inline void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
-                               uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ inline void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// byte offset of 16-byte chunk c of row r inside a [rows][BK] bf16 tile
-// (64-byte rows; XOR swizzle keeps ldmatrix conflict-free)
-__device__ inline uint32_t tile_off(int r, int c) {
-    return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
-}
-
-__global__ void __launch_bounds__(256, 1)
-k_oz_gemm(int n, int ncol, OzLayout o, const void* __restrict__ wsp, double* __restrict__ Z,
-          int ldz) {
-    extern __shared__ __align__(128) unsigned char smem[];
+__global__ void __launch_bounds__(kThreads, 1)
+k_oz_gemm(int n, int ncol, OzLayout o, const __grid_constant__ CUtensorMap mapA,
+          const __grid_constant__ CUtensorMap mapB, const void* __restrict__ wsp,
+          double* __restrict__ Z, int ldz, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf, acce, mdone;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    // 1024-byte aligned stage buffers (the swizzle atoms assume it)
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const char* wsb = static_cast<const char*>(wsp);
-    const __nv_bfloat16* gA = reinterpret_cast<const __nv_bfloat16*>(wsb + o.off_A);
-    const __nv_bfloat16* gB = reinterpret_cast<const __nv_bfloat16*>(wsb + o.off_B);
     const int* gE = reinterpret_cast<const int*>(wsb + o.off_E);
     const int* gF = reinterpret_cast<const int*>(wsb + o.off_F);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-    const int wm = warp & 1, wn = warp >> 1;  // warp tile 32 rows x 16 cols
-    const uint32_t sbase = smem_u32(smem);
     const int nK = o.Kp / BK;
+    const int nchunks = (nK + kChunkBlocks - 1) / kChunkBlocks;
 
-    auto load_stage = [&](int stage, int kt) {
-        const uint32_t st = sbase + stage * kStageBytes;
-        const int k0 = kt * BK;
-        // A: kS x 64 rows x 4 chunks; B: kS x 64 rows x 4 chunks
-        for (int idx = tid; idx < 2 * kS * 64 * 4; idx += 256) {
-            int c = idx & 3, r = (idx >> 2) & 63, t = idx >> 8;  // t in [0, 2 kS)
-            int i = t % kS;
-            bool isB = t >= kS;
-            const __nv_bfloat16* src =
-                isB ? gB + ((size_t)i * o.Np + n0 + r) * o.Kp + k0 + 8 * c
-                    : gA + ((size_t)i * o.Mp + m0 + r) * o.Kp + k0 + 8 * c;
-            uint32_t dst = st + (isB ? kS * kTileElems * 2 : 0) + i * kTileElems * 2 + tile_off(r, c);
-            cp_async16(dst, src);
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
         }
-    };
-
-    float acc[kS][2][2][4];
-    long long top[2][2][4];
-#pragma unroll
-    for (int d = 0; d < kS; ++d)
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[d][a][b][e] = 0.f;
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) top[a][b][e] = 0;
-
-    auto flush_top = [&]() {
-#pragma unroll
-        for (int d = 0; d < oz::kTopDiag; ++d)
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        top[a][b][e] += (long long)__float2int_rn(acc[d][a][b][e]) * (1LL << (8 * (oz::kTopDiag - 1 - d)));
-                        acc[d][a][b][e] = 0.f;
-                    }
-    };
-
-#pragma unroll
-    for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < nK) load_stage(s, s);
-        asm volatile("cp.async.commit_group;\n" ::);
+        tc::mbar_init(&accf, 1);
+        tc::mbar_init(&acce, kEpiWarps);
+        tc::mbar_init(&mdone, 1);
+        abort_flag = 0;
+        tc::mbar_fence_init();
     }
-    const int chunk_steps = kKc / BK;
-    for (int kt = 0; kt < nK; ++kt) {
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(STAGES - 2));
-        __syncthreads();
-        const uint32_t st = sbase + (kt % STAGES) * kStageBytes;
-        const uint32_t sA = st, sB = st + kS * kTileElems * 2;
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    int last_kb[STAGES];  // producer: last K slice loaded into each stage
 #pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-#pragma unroll
-            for (int i = 0; i < kS; ++i) {
-                uint32_t af[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    int mi = lane >> 3;
-                    int r = wm * 32 + mt * 16 + (mi & 1) * 8 + (lane & 7);
-                    int c = (kk >> 3) + (mi >> 1);
-                    ldsm_x4(sA + i * kTileElems * 2 + tile_off(r, c), af[mt][0], af[mt][1], af[mt][2],
-                            af[mt][3]);
+    for (int s = 0; s < STAGES; ++s) last_kb[s] = -1;
+
+    if (warp == 0) {
+        // ---- producer: TMA of the 7 digit matrices of A and B per K slice
+        if (lane == 0) {
+            for (int kb = 0; kb < nK && !abort_flag; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES && !tc::mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+                    abort_flag = 1;
+                    break;
                 }
+                unsigned char* st = smem + s * kStageBytes;
+                tc::mbar_expect_tx(&full[s], kStageBytes);
+                tc::tma_load_3d(st, &mapA, kb * BK, m0, 0, &full[s]);
+                tc::tma_load_3d(st + kABytes, &mapB, kb * BK, n0, 0, &full[s]);
+                last_kb[s] = kb;
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issue: 10 pieces x 2 K-steps per K slice
+        if (lane == 0) {
+            for (int kb = 0; kb < nK && !abort_flag; ++kb) {
+                const int s = kb % STAGES, c = kb / kChunkBlocks;
+                const bool chunk_start = kb % kChunkBlocks == 0;
+                if (!tc::mbar_wait(&full[s], (kb / STAGES) & 1)) {
+                    abort_flag = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t sa = tc::su32(smem + s * kStageBytes), sb = sa + kABytes;
+                for (int p = 0; p < kPieces; ++p) {
+                    if (p == kLowPieces && chunk_start && c > 0) {
+                        // diagonals 0..3 restart: wait until the epilogue has read them
+                        if (!tc::mbar_wait(&acce, (c - 1) & 1)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                    }
+                    const Piece pc = kPiece[p];
+                    const uint32_t idesc = tc::idesc_bf16(BM, BN * pc.nj);
+                    // the piece that zero-initialises its diagonals: {0,4,3} at
+                    // the first slice, {0,0,4} at the first slice of each chunk
+                    const bool init = pc.i == 0 && (pc.j0 == 0 ? chunk_start : kb == 0);
 #pragma unroll
-                for (int j = 0; j < kS - i; ++j) {
-                    uint32_t b0, b1, b2, b3;
-                    int mi = lane >> 3;
-                    int r = wn * 16 + (mi >> 1) * 8 + (lane & 7);
-                    int c = (kk >> 3) + (mi & 1);
-                    ldsm_x4(sB + j * kTileElems * 2 + tile_off(r, c), b0, b1, b2, b3);
+                    for (int ks = 0; ks < BK / 16; ++ks) {
+                        const uint64_t da = tc::smem_desc(sa + pc.i * (BM * BK * 2) + ks * 32, 512, 4);
+                        const uint64_t db = tc::smem_desc(sb + pc.j0 * (BN * BK * 2) + ks * 32, 512, 4);
+                        tc::mma_bf16(tmem + (pc.i + pc.j0) * BN, da, db, idesc,
+                                     (init && ks == 0) ? 0u : 1u);
+                    }
+                }
+                if (abort_flag) break;
+                tc::mma_commit(&empty[s]);
+                if (kb % kChunkBlocks == kChunkBlocks - 1 || kb == nK - 1) tc::mma_commit(&accf);
+            }
+        }
+    } else {
+        // ---- epilogue: lane quarter q of TMEM = rows 32q .. 32q+31 of the
+        // tile; half h of the 64 columns
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int row = m0 + 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + 32 * h;
+        long long top[32];
 #pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        mma_bf16(acc[i + j][mt][0], af[mt], b0, b1);
-                        mma_bf16(acc[i + j][mt][1], af[mt], b2, b3);
+        for (int c = 0; c < 32; ++c) top[c] = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!tc::mbar_wait(&accf, c & 1)) {
+                ok = false;
+                abort_flag = 1;
+                break;
+            }
+            tc::tc_fence_after();
+#pragma unroll
+            for (int d = 0; d < oz::kTopDiag; ++d) {
+                uint32_t v[2][16];
+                tc::tmem_ld16(tl + d * BN, v[0]);
+                tc::tmem_ld16(tl + d * BN + 16, v[1]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 32; ++t)
+                    top[t] += (long long)__float2int_rn(__uint_as_float(v[t >> 4][t & 15]))
+                              << (8 * (oz::kTopDiag - 1 - d));
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (c + 1 < nchunks && lane == 0) tc::mbar_arrive(&acce);
+        }
+        if (ok) {
+            // the remaining diagonals (FP32 over all of K) and the recombination
+            // 2^(E+F-14) (top 2^-24 + S4 2^-32 + S5 2^-40 + S6 2^-48)
+            const int er = row < n ? gE[row] : 0;
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                uint32_t v4[16], v5[16], v6[16];
+                tc::tmem_ld16(tl + 4 * BN + c0, v4);
+                tc::tmem_ld16(tl + 5 * BN + c0, v5);
+                tc::tmem_ld16(tl + 6 * BN + c0, v6);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int col = n0 + 32 * h + c0 + t;
+                    if (row < n && col < ncol) {
+                        double v = (double)top[c0 + t] * 0x1p-24;
+                        v = fma((double)__uint_as_float(v4[t]), 0x1p-32, v);
+                        v = fma((double)__uint_as_float(v5[t]), 0x1p-40, v);
+                        v = fma((double)__uint_as_float(v6[t]), 0x1p-48, v);
+                        Z[row + (size_t)col * ldz] = scalbn(v, er + gF[col] - 14);
                     }
                 }
             }
         }
-        const int nxt = kt + STAGES - 1;
-        if (nxt < nK) load_stage(nxt % STAGES, nxt);
-        asm volatile("cp.async.commit_group;\n" ::);
-        if ((kt + 1) % chunk_steps == 0) flush_top();
     }
-    if (nK % chunk_steps != 0) flush_top();
-    asm volatile("cp.async.wait_group 0;\n" ::);
-
-    // recombination: 2^(E+F-14) (top 2^-24 + S4 2^-32 + S5 2^-40 + S6 2^-48)
-    const int g = lane >> 2, t4 = lane & 3;
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1 && lane == 0) {
+        // every MMA this thread issued has retired before TMEM is released
+        tc::mma_commit(&mdone);
+        if (!tc::mbar_wait(&mdone, 0)) abort_flag = 1;
+    }
+    if (warp == 0 && lane == 0 && abort_flag) {
+        // after an abort, let the copies still in flight land (bounded wait)
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int r = m0 + wm * 32 + mt * 16 + g + ((e >> 1) << 3);
-                const int c = n0 + wn * 16 + nt * 8 + 2 * t4 + (e & 1);
-                if (r < n && c < ncol) {
-                    double v = (double)top[mt][nt][e] * 0x1p-24;
-                    v = fma((double)acc[4][mt][nt][e], 0x1p-32, v);
-                    v = fma((double)acc[5][mt][nt][e], 0x1p-40, v);
-                    v = fma((double)acc[6][mt][nt][e], 0x1p-48, v);
-                    Z[r + (size_t)c * ldz] = scalbn(v, gE[r] + gF[c] - 14);
-                }
-            }
+        for (int s = 0; s < STAGES; ++s)
+            if (last_kb[s] >= 0) tc::mbar_wait(&full[s], (last_kb[s] / STAGES) & 1);
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicMin(err, -5);  // reported as HSEIN_ECUDA
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
 }
 
 }  // namespace
 
-size_t ozq0_workspace_bytes(int n, int ncol) { return oz_layout(n, ncol).total; }
+size_t ozq0_workspace_bytes(int n, int ncol) { return oz_layout(n, ncol).total + 256; }
 
-void launch_ozaki_q0(int n, int ncol, const double* Q, int ldq, const double* X, int ldx,
-                     double* Z, int ldz, void* ws, cudaStream_t s) {
+bool launch_ozaki_q0(int n, int ncol, const double* Q, int ldq, const double* X, int ldx,
+                     double* Z, int ldz, void* ws, int* err, cudaStream_t s) {
     const OzLayout o = oz_layout(n, ncol);
     char* w = static_cast<char*>(ws);
     unsigned long long* rmax = reinterpret_cast<unsigned long long*>(w + o.off_rmax);
@@ -295,8 +332,19 @@ void launch_ozaki_q0(int n, int ncol, const double* Q, int ldq, const double* X,
     dim3 g1(o.Mp / 32, o.Kp / 32);
     k_oz_split_rows<<<g1, dim3(32, 8), 0, s>>>(n, n, Q, ldq, rmax, E, dA, o.Mp, o.Kp);
     k_oz_split_cols<<<o.Np, 256, 0, s>>>(n, ncol, X, ldx, F, dB, o.Np, o.Kp);
+    CUtensorMap mA, mB;
+    const uint64_t dimA[3] = {(uint64_t)o.Kp, (uint64_t)o.Mp, (uint64_t)kS};
+    const uint64_t strA[2] = {(uint64_t)o.Kp * 2, (uint64_t)o.Mp * o.Kp * 2};
+    const uint32_t boxA[3] = {BK, BM, kS};
+    const uint64_t dimB[3] = {(uint64_t)o.Kp, (uint64_t)o.Np, (uint64_t)kS};
+    const uint64_t strB[2] = {(uint64_t)o.Kp * 2, (uint64_t)o.Np * o.Kp * 2};
+    const uint32_t boxB[3] = {BK, BN, kS};
+    if (!encode_bf16_map_3d(&mA, dA, dimA, strA, boxA, 64) ||
+        !encode_bf16_map_3d(&mB, dB, dimB, strB, boxB, 64))
+        return false;
     dim3 g2(o.Np / BN, o.Mp / BM);
-    k_oz_gemm<<<g2, 256, kSmemBytes, s>>>(n, ncol, o, ws, Z, ldz);
+    k_oz_gemm<<<g2, kThreads, kSmemBytes, s>>>(n, ncol, o, mA, mB, ws, Z, ldz, err);
+    return true;
 }
 
 cudaError_t ozaki_configure() {

@@ -67,8 +67,10 @@ __device__ inline void split_digits(double a, int E, int* d) {
 
 // host launchers
 size_t ozq0_workspace_bytes(int n, int ncol);
-void launch_ozaki_q0(int n, int ncol, const double* Q, int ldq, const double* X, int ldx,
-                     double* Z, int ldz, void* ws, cudaStream_t s);
+// false if the TMA tensor maps could not be encoded; a device-side abort
+// (a wait that timed out) lowers *err to -5
+bool launch_ozaki_q0(int n, int ncol, const double* Q, int ldq, const double* X, int ldx,
+                     double* Z, int ldz, void* ws, int* err, cudaStream_t s);
 cudaError_t ozaki_configure();
 
 }  // namespace hsein
