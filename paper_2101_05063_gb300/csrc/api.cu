@@ -32,6 +32,12 @@ struct hsein_plan_s {
     Layout L;
     hsein_options opt;
     int device;
+    int num_sms = 0;
+    // split precision: TMA tensor maps of the digit operands, encoded for the
+    // workspace address they were last used with
+    const void* maps_work = nullptr;
+    std::vector<CUtensorMap> mapsA;
+    CUtensorMap mapB;
     // measurement: one (phase, start, end) record per launch while enabled
     int profiling = 0;
     std::vector<cudaEvent_t> pool;
@@ -163,6 +169,7 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
     make_layout(&p->L, n, m_real, m_cplx, o.br, o.precision);
     p->opt = o;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
         hsein::diag_configure(o.br) != cudaSuccess || hsein::update_configure(o.br) != cudaSuccess ||
         hsein::ozaki_configure() != cudaSuccess || hsein::update_oz_configure() != cudaSuccess) {
         cudaGetLastError();
@@ -199,6 +206,14 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
         return HSEIN_EARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int robust = plan->opt.robust, om = plan->opt.omega_log2;
+    if (L.oz && plan->maps_work != dWork) {
+        plan->mapsA.resize(L.N);
+        if (!hsein::encode_update_oz_maps(L, dWork, plan->mapsA.data(), &plan->mapB)) {
+            plan->maps_work = nullptr;
+            return HSEIN_ECUDA;
+        }
+        plan->maps_work = dWork;
+    }
     {
         PhaseScope ps(plan, 0, s);
         hsein::launch_prepare(L, dWork, dH, ldh, dWr, dWi, dB, ldb, om, s);
@@ -212,7 +227,7 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
         }
         PhaseScope ps(plan, 2, s);
         if (L.oz)
-            hsein::launch_update_oz(L, dWork, J, s);
+            hsein::launch_update_oz(L, dWork, J, plan->num_sms, plan->mapsA[J], plan->mapB, s);
         else
             hsein::launch_update(L, dWork, dH, ldh, J, s);
     }

@@ -28,6 +28,8 @@
 // column count to a multiple of 32.
 #pragma once
 
+#include <cuda.h>
+
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -106,7 +108,11 @@ void launch_prepare(const Layout& L, void* work, const double* H, int ldh, const
 void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, int robust,
                  int omega_log2, cudaStream_t s);
 void launch_update(const Layout& L, void* work, const double* H, int ldh, int J, cudaStream_t s);
-void launch_update_oz(const Layout& L, void* work, int J, cudaStream_t s);
+// split-precision update: tensor maps of the A_J digit blocks (mapsA[1..N-1])
+// and of the [Z'|W] digits for the workspace at `work`
+bool encode_update_oz_maps(const Layout& L, void* work, CUtensorMap* mapsA, CUtensorMap* mapB);
+void launch_update_oz(const Layout& L, void* work, int J, int num_sms, const CUtensorMap& mapA,
+                      const CUtensorMap& mapB, cudaStream_t s);
 void launch_stage_tiles(const Layout& L, void* work, const double* H, int ldh, cudaStream_t s);
 void launch_split_h(const Layout& L, void* work, const double* H, int ldh, cudaStream_t s);
 size_t oz_update_hd_elems(const Layout& L);

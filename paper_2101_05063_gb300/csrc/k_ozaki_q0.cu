@@ -246,7 +246,7 @@ k_oz_gemm(int n, int ncol, OzLayout o, const __grid_constant__ CUtensorMap mapA,
         for (int c = 0; c < 32; ++c) top[c] = 0;
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
-            if (!tc::mbar_wait(&accf, c & 1)) {
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&accf, c & 1))) {
                 ok = false;
                 abort_flag = 1;
                 break;

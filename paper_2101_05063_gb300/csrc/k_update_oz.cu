@@ -6,24 +6,37 @@
 //                 rows of different magnitude keep their own scale.
 //  k_update_oz    A_J [Z'|W] from the digit products of A_J and of the
 //                 [Z'|W] digits k_diag wrote (one exponent per product
-//                 column), on the BF16 tensor cores (mma.sync m16n8k16,
-//                 FP32 accumulation).  With K = b_r = 64 every diagonal sum
-//                 stays below 2^24 (7 x 64 x 2^14), so all of them are exact
-//                 integers; they are folded into two int64 and recombined in
-//                 FP64 once per output.  The epilogue is that of the FP64
-//                 k_update (eq. "robust-update" and the cross-over reduction
-//                 of Alg. "tiled-reduction2").
+//                 column), on the 5th-generation tensor cores: TMA brings
+//                 the seven 128 x 64 digit tiles of A_J into shared memory
+//                 once per CTA and streams 32-column digit tiles of [Z'|W]
+//                 through two stages; one thread issues tcgen05.mma (BF16 x
+//                 BF16 -> FP32) into seven diagonal accumulators in TMEM,
+//                 double-buffered so that the epilogue of one tile overlaps
+//                 the products of the next.  With K = b_r = 64 every diagonal
+//                 sum stays below 2^24 (7 x 64 x 2^14), so all of them are
+//                 exact integers; they are folded into two int64 and
+//                 recombined in FP64 once per output.  The epilogue is that
+//                 of the FP64 k_update (the robust update of Sec. 3 and the
+//                 cross-over reduction of the tiled algorithm).
 #include "common.cuh"
 #include "ozaki.cuh"
+#include "tc.cuh"
+
+#include <algorithm>
 
 namespace hsein {
 namespace {
 
 using oz::kS;
 constexpr int kBr = 64;  // tile height this path supports
-constexpr int BM = 64, BN = 64;
-constexpr int kTile = BM * kBr;  // bf16 elements of one digit tile (64 rows x 64 k)
-constexpr int kSmem = 2 * kS * kTile * 2;
+constexpr int TBM = 128;  // rows of A_J per tile (the TMEM lanes)
+constexpr int TBN = 32;   // product columns per tile (16 solution columns)
+constexpr int kABytes = kS * TBM * kBr * 2;  // seven 128 x 64 digit tiles of A_J
+constexpr int kBBytes = kS * TBN * kBr * 2;  // seven 32 x 64 digit tiles of [Z'|W]
+constexpr int kSmem = kABytes + 2 * kBBytes + 1024;  // + alignment slack
+constexpr int kAccCols = 256;  // one accumulator set: 7 diagonals x 32 columns, padded
+constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, one 8-column group each
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA issuer, epilogue
 
 __global__ void k_oz_split_h(Layout L, void* work, const double* __restrict__ H, int ldh) {
     const DevState* st = ws<DevState>(work, L.off_state);
@@ -71,229 +84,313 @@ __global__ void k_oz_split_h(Layout L, void* work, const double* __restrict__ H,
     }
 }
 
-__device__ inline uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ inline void cp_async16_zfill(uint32_t dst, const void* src, bool valid) {
-    int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n));
-}
-__device__ inline void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
-                               uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-__device__ inline void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// 128-byte rows (64 bf16), 8 chunks of 16 bytes, XOR swizzle by row
-__device__ inline uint32_t tile_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
-// exact recombination: 2^(e-14) sum_d 2^(-8d) S_d from the exact FP32 sums
-__device__ inline double combine(const float (&acc)[kS][2][2][4], int mt, int nt, int el, int e) {
-    long long top = 0, low = 0;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) top += (long long)__float2int_rn(acc[d][mt][nt][el]) * (1LL << (8 * (3 - d)));
-#pragma unroll
-    for (int d = 4; d < kS; ++d) low += (long long)__float2int_rn(acc[d][mt][nt][el]) * (1LL << (8 * (kS - 1 - d)));
-    double v = fma((double)low, 0x1p-24, (double)top);  // in units of 2^-24 of the top
-    return scalbn(v, e - 14 - 24);
+// RN(top + low 2^-24) 2^k from the two exact integer parts, built with
+// integer operations only (GB300's FP64 pipe is the scarce resource of the
+// epilogue).  |top| < 2^45 and |low| < 2^39, so V = top 2^24 + low has at
+// most 70 bits.  While |top| < 2^38, V fits a 64-bit integer as it is;
+// beyond, W = |V| >> 7 with the dropped bits OR-ed into its last bit (a
+// rounding to odd with at least 55 bits, whose rounding to 53 bits is the
+// rounding of V).  Results outside the normal range take scalbn.
+__device__ inline double fixed_to_double(long long top, long long low, int k) {
+    const bool big = (unsigned long long)(top + (1LL << 38)) >= (1ULL << 39);
+    bool neg;
+    unsigned long long M;
+    int sh;
+    if (!big) {
+        const long long V = top * (1LL << 24) + low;
+        neg = V < 0;
+        M = (unsigned long long)(neg ? -V : V);
+        sh = 0;
+    } else {
+        neg = top < 0;
+        const long long t = neg ? -top : top, l = neg ? -low : low;  // |V| = t 2^24 + l
+        M = (unsigned long long)(t * (1LL << 17) + (l >> 7)) | ((l & 127) != 0 ? 1ULL : 0ULL);
+        sh = 7;
+    }
+    if (M == 0) return 0.0;
+    const int lz = __clzll((long long)M);
+    const unsigned long long Mn = M << lz;  // leading bit at 63
+    unsigned long long mant = Mn >> 11;     // 53 bits
+    const unsigned rb = (unsigned)(Mn & 0x7FF);
+    if (rb > 0x400u || (rb == 0x400u && (mant & 1))) ++mant;  // to nearest, ties to even
+    const int E = (63 - lz) + sh - 24 + k;  // value = (mant / 2^52) 2^E
+    if (E >= -1022 && E <= 1022) {
+        // the implicit bit of mant (or its carry to 2^53) lands in the exponent field
+        const unsigned long long bits =
+            ((unsigned long long)neg << 63) + ((unsigned long long)(E + 1022) << 52) + mant;
+        return __longlong_as_double((long long)bits);
+    }
+    const double m = (double)mant;
+    return scalbn(neg ? -m : m, E - 52);
 }
 
-__global__ void __launch_bounds__(256, 1)
-k_update_oz(Layout L, void* work, int J) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const DevState* st = ws<DevState>(work, L.off_state);
+// exact recombination of product column c from its seven diagonal sums
+// (FP32 bit patterns read from TMEM): 2^(e-14) sum_d 2^(-8d) S_d.  With
+// |S_d| <= (d+1) 64 2^14 the pairs S_0 256 + S_1, S_2 256 + S_3 and
+// S_4 256 + S_5 fit in 32-bit integers.
+__device__ inline double recombine(const uint32_t (&a)[kS][4], int c, int e) {
+    int S[kS];
+#pragma unroll
+    for (int d = 0; d < kS; ++d) S[d] = __float2int_rn(__uint_as_float(a[d][c]));
+    const int t1 = S[0] * 256 + S[1], t2 = S[2] * 256 + S[3], t3 = S[4] * 256 + S[5];
+    const long long top = (long long)t1 * 65536 + t2;  // |top| < 2^45
+    const long long low = (long long)t3 * 256 + S[6];  // |low| < 2^39
+    return fixed_to_double(top, low, e - 14 - 24);
+}
+
+// an upper bound of |v| as the high word of its bit pattern, rounded up
+// (orders like the magnitude; (bound << 32) reads back as a double >= |v|)
+__device__ inline uint32_t mag_hi(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+    return (uint32_t)(b >> 32) + ((uint32_t)b != 0 ? 1u : 0u);
+}
+
+__host__ __device__ inline size_t hd_block(const Layout& L, int J) {
+    // rows of all blocks A_1 .. A_{J-1} before block J
+    return (size_t)(J - 1) * L.b0 + (size_t)kBr * (J - 1) * (J - 2) / 2;
+}
+
+// grid: x = 128-row tiles of A_J, y = groups of tiles_per_cta consecutive
+// 32-column tiles of [Z'|W]
+__global__ void __launch_bounds__(kThreads, 1)
+k_update_oz(Layout L, void* work, int J, int tiles_per_cta, const __grid_constant__ CUtensorMap mapA,
+            const __grid_constant__ CUtensorMap mapB) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t afull, bfull[2], bempty[2], tfull[2], tempty[2], mdone;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    DevState* st = ws<DevState>(work, L.off_state);
     if (st->status < 0) return;
     const int p0 = tile_start(L, J);
-    const int r0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;
-    const size_t P = (size_t)(J - 1) * L.b0 + (size_t)kBr * (J - 1) * (J - 2) / 2;
-    const __nv_bfloat16* hd = ws<__nv_bfloat16>(work, L.off_hd) + kS * kBr * P;
-    const int* he = ws<int>(work, L.off_he) + P;
-    const __nv_bfloat16* zd = ws<__nv_bfloat16>(work, L.off_zwd);
-    const int* zf = ws<int>(work, L.off_zwf);
-    const int ncz = 2 * L.ncolp;
-    const uint32_t sA = smem_u32(smem), sB = sA + kS * kTile * 2;
-    for (int idx = tid; idx < 2 * kS * 64 * 8; idx += 256) {
-        int c = idx & 7, r = (idx >> 3) & 63, t = idx >> 9;  // t in [0, 2 kS)
-        if (t < kS) {
-            bool ok = r0 + r < p0;
-            const __nv_bfloat16* src = hd + ((size_t)t * p0 + (ok ? r0 + r : 0)) * kBr + 8 * c;
-            cp_async16_zfill(sA + t * kTile * 2 + tile_off(r, c), src, ok);
-        } else {
-            int i = t - kS;
-            const __nv_bfloat16* src = zd + ((size_t)i * ncz + n0 + r) * kBr + 8 * c;
-            cp_async16_zfill(sB + i * kTile * 2 + tile_off(r, c), src, true);
-        }
-    }
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncthreads();
+    const int m0 = blockIdx.x * TBM;
+    const int t_begin = blockIdx.y * tiles_per_cta;
+    const int ntl = min(2 * L.ncolp / TBN - t_begin, tiles_per_cta);
+    if (ntl <= 0) return;
+    unsigned char* sA = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* sB = sA + kABytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    float acc[kS][2][2][4];
-#pragma unroll
-    for (int d = 0; d < kS; ++d)
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[d][a][b][e] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < kBr; kk += 16) {
-#pragma unroll
-        for (int i = 0; i < kS; ++i) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                int mi = lane >> 3;
-                int r = wm * 32 + mt * 16 + (mi & 1) * 8 + (lane & 7);
-                int c = (kk >> 3) + (mi >> 1);
-                ldsm_x4(sA + i * kTile * 2 + tile_off(r, c), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
+    if (tid == 0) {
+        tc::mbar_init(&afull, 1);
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&bfull[s], 1);
+            tc::mbar_init(&bempty[s], 1);
+            tc::mbar_init(&tfull[s], 1);
+            tc::mbar_init(&tempty[s], kEpiWarps);
+        }
+        tc::mbar_init(&mdone, 1);
+        abort_flag = 0;
+        tc::mbar_fence_init();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, 2 * kAccCols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    int last_t[2] = {-1, -1};  // producer: last tile loaded into each B stage
+
+    if (warp == 0) {
+        // ---- producer: A_J digits once, [Z'|W] digit tiles through two stages
+        if (lane == 0) {
+            tc::mbar_expect_tx(&afull, kABytes);
+            tc::tma_load_3d(sA, &mapA, 0, m0, 0, &afull);
+            for (int t = 0; t < ntl && !abort_flag; ++t) {
+                const int s = t & 1;
+                if (t >= 2 && !tc::mbar_wait(&bempty[s], ((t >> 1) - 1) & 1)) {
+                    abort_flag = 1;
+                    break;
+                }
+                tc::mbar_expect_tx(&bfull[s], kBBytes);
+                tc::tma_load_3d(sB + s * kBBytes, &mapB, 0, (t_begin + t) * TBN, 0, &bfull[s]);
+                last_t[s] = t;
             }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issue: A digit i against B digits 0..6-i in one MMA of
+        // N = 32 (7 - i), written to the diagonal accumulators i .. 6
+        if (lane == 0) {
+            if (!tc::mbar_wait(&afull, 0)) abort_flag = 1;
+            for (int t = 0; t < ntl && !abort_flag; ++t) {
+                const int s = t & 1;
+                if (!tc::mbar_wait(&bfull[s], (t >> 1) & 1) ||
+                    (t >= 2 && !tc::mbar_wait(&tempty[s], ((t >> 1) - 1) & 1))) {
+                    abort_flag = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t sa = tc::su32(sA), sb = tc::su32(sB + s * kBBytes);
 #pragma unroll
-            for (int j = 0; j < kS - i; ++j) {
-                uint32_t b0, b1, b2, b3;
-                int mi = lane >> 3;
-                int r = wn * 16 + (mi >> 1) * 8 + (lane & 7);
-                int c = (kk >> 3) + (mi & 1);
-                ldsm_x4(sB + j * kTile * 2 + tile_off(r, c), b0, b1, b2, b3);
+                for (int i = 0; i < kS; ++i) {
+                    const uint32_t idesc = tc::idesc_bf16(TBM, TBN * (kS - i));
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    mma_bf16(acc[i + j][mt][0], af[mt], b0, b1);
-                    mma_bf16(acc[i + j][mt][1], af[mt], b2, b3);
+                    for (int ks = 0; ks < kBr / 16; ++ks) {
+                        const uint64_t da = tc::smem_desc(sa + i * (TBM * kBr * 2) + ks * 32, 1024, 2);
+                        const uint64_t db = tc::smem_desc(sb + ks * 32, 1024, 2);
+                        tc::mma_bf16(tmem + s * kAccCols + i * TBN, da, db, idesc,
+                                     (i == 0 && ks == 0) ? 0u : 1u);
+                    }
+                }
+                tc::mma_commit(&bempty[s]);
+                tc::mma_commit(&tfull[s]);
+            }
+        }
+    } else {
+        // ---- epilogue: TMEM lane quarter q = rows 32q .. 32q+31 of the tile,
+        // one row per thread; warp group g takes product columns 8g .. 8g+7
+        // (4 solution columns).  The element-wise update is that of the FP64
+        // k_update.
+        const int q = warp & 3, g = (warp - 2) >> 2;
+        const int gi = m0 + 32 * q + lane;
+        const bool rv = gi < p0, last = gi == p0 - 1;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        const Epi* epi = ws<Epi>(work, L.off_epi);
+        double* X = ws<double>(work, L.off_X);
+        double* R = ws<double>(work, L.off_R);
+        const int* zf = ws<int>(work, L.off_zwf);
+        const int ea = rv ? ws<int>(work, L.off_he)[hd_block(L, J) + gi] : 0;
+        unsigned long long* bmax = ws<unsigned long long>(work, L.off_bmax);
+        unsigned long long* rmax = ws<unsigned long long>(work, L.off_rmax);
+        const size_t ldw = L.ldw;
+        for (int t = 0; t < ntl; ++t) {
+            const int s = t & 1;
+            const int gc = (t_begin + t) * TBN + 8 * g;  // first product column of the group
+            const int sc = gc >> 1;                      // its first solution column
+            // operands that do not depend on the products: issued before the wait
+            int ez[8];
+            {
+                const int4 z0 = *reinterpret_cast<const int4*>(zf + gc);
+                const int4 z1 = *reinterpret_cast<const int4*>(zf + gc + 4);
+                ez[0] = ea + z0.x, ez[1] = ea + z0.y, ez[2] = ea + z0.z, ez[3] = ea + z0.w;
+                ez[4] = ea + z1.x, ez[5] = ea + z1.y, ez[6] = ea + z1.z, ez[7] = ea + z1.w;
+            }
+            double xv[4], rv4[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool ok = rv && sc + k < L.ncol;
+                const size_t ix = gi + (size_t)(sc + k) * ldw;
+                xv[k] = ok ? X[ix] : 0.0;
+                rv4[k] = ok ? R[ix] : 0.0;
+            }
+            if (lane < 2) {
+                // the group's shift parameters (at most 4 consecutive entries)
+                const int q0 = sc < 2 * L.mc ? (sc >> 1) : L.mc + (sc - 2 * L.mc);
+                if (q0 < L.m) {
+                    const char* pf = reinterpret_cast<const char*>(epi + q0) + 128 * lane;
+                    asm volatile("prefetch.global.L1 [%0];\n" ::"l"(pf));
                 }
             }
-        }
-    }
-
-    // ---------------- epilogue (as in k_update) ---------------------------
-    const Epi* epi = ws<Epi>(work, L.off_epi);
-    double* X = ws<double>(work, L.off_X);
-    double* R = ws<double>(work, L.off_R);
-    const int g = lane >> 2, t4 = lane & 3;
-    double mb[2] = {0.0, 0.0}, mr[2] = {0.0, 0.0};  // per n-tile
-    double nb[2][2][2], nr[2][2][2];                // [mt][nt][row half]
-    int gis[2][2];
-    // phase A: all loads and arithmetic
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&tfull[s], (t >> 1) & 1))) {
+                abort_flag = 1;
+                break;
+            }
+            tc::tc_fence_after();
+            uint32_t mb[4] = {0, 0, 0, 0}, mr[4] = {0, 0, 0, 0};
+            // two halves of 4 product columns: one pair of solution columns each
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-        const int gc = n0 + wn * 16 + nt * 8 + 2 * t4;  // product column of Z'
-        const int sc = gc >> 1;                          // solution column
-        const bool valid_col = sc < L.ncol;
-        const bool cplx = sc < 2 * L.mc;
-        const int q = cplx ? (sc >> 1) : L.mc + (sc - 2 * L.mc);
-        const bool is_im = cplx && (sc & 1);
-        const int scre = cplx ? (sc & ~1) : sc;
-        Epi E;
-        if (valid_col) E = epi[q];
-        const int fz = zf[gc], fw = zf[gc + 1];
+            for (int u = 0; u < 2; ++u) {
+                uint32_t a[kS][4];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+                for (int d = 0; d < kS; ++d)
+                    tc::tmem_ld4(tl + s * kAccCols + d * TBN + 8 * g + 4 * u, a[d]);
+                tc::tmem_wait_ld();
+                if (u == 1) {
+                    // this warp is done with the accumulator set
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&tempty[s]);
+                }
+                double z[4];  // A_J Z' and A_J W of the pair, interleaved
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = wm * 32 + mt * 16 + g + 8 * h;
-                const int gi = r0 + row;
-                gis[mt][h] = gi;
-                nb[mt][nt][h] = 0.0;
-                nr[mt][nt][h] = 0.0;
-                if (!(valid_col && gi < p0)) continue;
-                const int ea = he[gi];
-                const double az = combine(acc, mt, nt, 2 * h, ea + fz);
-                const double aw = combine(acc, mt, nt, 2 * h + 1, ea + fw);
-                const bool last = gi == p0 - 1;
-                const double b_ = X[gi + (size_t)sc * L.ldw];
-                if (cplx) {
-                    const double ur = R[gi + (size_t)scre * L.ldw];
-                    const double ui = R[gi + (size_t)(scre + 1) * L.ldw];
-                    const double u = is_im ? ui : ur;
-                    // z_br (complex) times R~: re = ur zr - ui zi, im = ur zi + ui zr
-                    double rz = is_im ? (ur * E.zbr_im + ui * E.zbr_re) : (ur * E.zbr_re - ui * E.zbr_im);
-                    double vb = fma(b_, E.fB, -az) - rz;
-                    double vr = fma(E.pi, u, aw);
+                for (int c = 0; c < 4; ++c) z[c] = recombine(a, c, ez[4 * u + c]);
+                const int sp = sc + 2 * u;  // even solution column of the pair
+                if (!rv || sp >= L.ncol) continue;
+                if (sp < 2 * L.mc) {
+                    // complex pair (re, im) of one shift; z_br (complex) times R~
+                    const Epi E = epi[sp >> 1];
+                    const size_t ir = gi + (size_t)sp * ldw, ii = ir + ldw;
+                    const double ur = rv4[2 * u], ui = rv4[2 * u + 1], br = xv[2 * u], bi = xv[2 * u + 1];
+                    double vbr = fma(ui, E.zbr_im, fma(-ur, E.zbr_re, fma(br, E.fB, -z[0])));
+                    double vbi = fma(-ui, E.zbr_re, fma(-ur, E.zbr_im, fma(bi, E.fB, -z[2])));
+                    double vrr = fma(E.pi, ur, z[1]), vri = fma(E.pi, ui, z[3]);
                     if (last) {
-                        vb += is_im ? E.cz_im : E.cz_re;
-                        vr -= is_im ? E.cw_im : E.cw_re;
+                        vbr += E.cz_re;
+                        vbi += E.cz_im;
+                        vrr -= E.cw_re;
+                        vri -= E.cw_im;
                     }
-                    nb[mt][nt][h] = vb;
-                    nr[mt][nt][h] = vr;
+                    X[ir] = vbr;
+                    X[ii] = vbi;
+                    R[ir] = vrr;
+                    R[ii] = vri;
+                    mb[2 * u] = mag_hi(vbr);
+                    mb[2 * u + 1] = mag_hi(vbi);
+                    mr[2 * u] = mag_hi(vrr);
+                    mr[2 * u + 1] = mag_hi(vri);
                 } else {
-                    const double u = R[gi + (size_t)sc * L.ldw];
-                    double vb = fma(b_, E.fB, -az) - u * E.zbr_re;
-                    double vr = fma(E.pi, u, aw);
-                    if (last) {
-                        vb += E.cz_re;
-                        vr -= E.cw_re;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int sk = sp + k;
+                        if (sk >= L.ncol) break;
+                        const Epi E = epi[L.mc + (sk - 2 * L.mc)];
+                        const size_t ix = gi + (size_t)sk * ldw;
+                        const double u_ = rv4[2 * u + k];
+                        double vb = fma(-u_, E.zbr_re, fma(xv[2 * u + k], E.fB, -z[2 * k]));
+                        double vr = fma(E.pi, u_, z[2 * k + 1]);
+                        if (last) {
+                            vb += E.cz_re;
+                            vr -= E.cw_re;
+                        }
+                        X[ix] = vb;
+                        R[ix] = vr;
+                        mb[2 * u + k] = mag_hi(vb);
+                        mr[2 * u + k] = mag_hi(vr);
                     }
-                    nb[mt][nt][h] = vb;
-                    nr[mt][nt][h] = vr;
-                }
-                mb[nt] = fmax(mb[nt], fabs(nb[mt][nt][h]));
-                mr[nt] = fmax(mr[nt], fabs(nr[mt][nt][h]));
-            }
-    }
-    __syncwarp();  // every lane has read R~ before any lane overwrites it
-    // phase B: stores
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-        const int sc = (n0 + wn * 16 + nt * 8 + 2 * t4) >> 1;
-        if (sc >= L.ncol) continue;
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int gi = gis[mt][h];
-                if (gi < p0) {
-                    X[gi + (size_t)sc * L.ldw] = nb[mt][nt][h];
-                    R[gi + (size_t)sc * L.ldw] = nr[mt][nt][h];
                 }
             }
-    }
-    // per-shift maxima: over the 8 row groups of the warp, then the 2 row warps
+            {
+                // per-shift maxima over the warp's 32 rows; lanes 0..7 post them
+                uint32_t mine = 0;
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            mb[nt] = fmax(mb[nt], __shfl_xor_sync(0xffffffffu, mb[nt], o));
-            mr[nt] = fmax(mr[nt], __shfl_xor_sync(0xffffffffu, mr[nt], o));
-        }
-    __syncthreads();
-    double* red = reinterpret_cast<double*>(smem);  // [2 wm][2 kinds][32 solution cols]
-    if (g == 0) {
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            int cl = wn * 8 + nt * 4 + t4;  // solution column within the tile (0..31)
-            red[(wm * 2 + 0) * 32 + cl] = mb[nt];
-            red[(wm * 2 + 1) * 32 + cl] = mr[nt];
+                for (int v = 0; v < 8; ++v) {
+                    const uint32_t m = __reduce_max_sync(0xffffffffu, v < 4 ? mb[v] : mr[v - 4]);
+                    if (lane == v) mine = m;
+                }
+                const int sv = sc + (lane & 3);
+                if (lane < 8 && sv < L.ncol && mine != 0) {
+                    const int qq = sv < 2 * L.mc ? (sv >> 1) : L.mc + (sv - 2 * L.mc);
+                    atomicMax((lane >> 2 ? rmax : bmax) + qq, (unsigned long long)mine << 32);
+                }
+            }
         }
     }
+    tc::tc_fence_before();
     __syncthreads();
-    if (tid < 64) {
-        const int which = tid >> 5, cl = tid & 31;
-        double v = fmax(red[(0 * 2 + which) * 32 + cl], red[(1 * 2 + which) * 32 + cl]);
-        const int sc = (n0 >> 1) + cl;
-        if (sc < L.ncol) {
-            int q = sc < 2 * L.mc ? (sc >> 1) : L.mc + (sc - 2 * L.mc);
-            unsigned long long* dst = ws<unsigned long long>(work, which ? L.off_rmax : L.off_bmax);
-            atomic_max_nonneg(dst + q, v);
-        }
+    if (warp == 1 && lane == 0) {
+        // every MMA this thread issued has retired before TMEM is released
+        tc::mma_commit(&mdone);
+        if (!tc::mbar_wait(&mdone, 0)) abort_flag = 1;
+    }
+    if (warp == 0 && lane == 0 && abort_flag) {
+        // after an abort, let the copies still in flight land (bounded waits)
+        tc::mbar_wait(&afull, 0);
+        for (int s = 0; s < 2; ++s)
+            if (last_t[s] >= 0) tc::mbar_wait(&bfull[s], (last_t[s] >> 1) & 1);
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) set_error(st, -5);  // HSEIN_ECUDA
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 2 * kAccCols);
     }
 }
 
 }  // namespace
 
 size_t oz_update_hd_elems(const Layout& L) {
-    const size_t Nm1 = (size_t)L.N;  // P(N) = sum over J = 1..N-1 of p0(J)
-    size_t P = (Nm1 - 1) * L.b0 + (size_t)kBr * (Nm1 - 1) * (Nm1 - 2) / 2;
-    if (L.N <= 1) P = 0;
-    return P;
+    // rows of all blocks A_1 .. A_{N-1}
+    return L.N <= 1 ? 0 : hd_block(L, L.N);
 }
 
 void launch_split_h(const Layout& L, void* work, const double* H, int ldh, cudaStream_t s) {
@@ -302,11 +399,39 @@ void launch_split_h(const Layout& L, void* work, const double* H, int ldh, cudaS
     k_oz_split_h<<<grid, dim3(32, 8), 0, s>>>(L, work, H, ldh);
 }
 
-void launch_update_oz(const Layout& L, void* work, int J, cudaStream_t s) {
+bool encode_update_oz_maps(const Layout& L, void* work, CUtensorMap* mapsA, CUtensorMap* mapB) {
+    const __nv_bfloat16* hd = ws<__nv_bfloat16>(work, L.off_hd);
+    for (int J = 1; J < L.N; ++J) {
+        const uint64_t p0 = (uint64_t)tile_start(L, J);
+        const uint64_t dims[3] = {(uint64_t)kBr, p0, (uint64_t)kS};
+        const uint64_t strides[2] = {(uint64_t)kBr * 2, p0 * kBr * 2};
+        const uint32_t box[3] = {(uint32_t)kBr, (uint32_t)TBM, (uint32_t)kS};
+        if (!encode_bf16_map_3d(&mapsA[J], hd + kS * kBr * hd_block(L, J), dims, strides, box, 128))
+            return false;
+    }
+    const uint64_t ncz = 2 * (uint64_t)L.ncolp;
+    const uint64_t dims[3] = {(uint64_t)kBr, ncz, (uint64_t)kS};
+    const uint64_t strides[2] = {(uint64_t)kBr * 2, ncz * kBr * 2};
+    const uint32_t box[3] = {(uint32_t)kBr, (uint32_t)TBN, (uint32_t)kS};
+    return encode_bf16_map_3d(mapB, ws<__nv_bfloat16>(work, L.off_zwd), dims, strides, box, 128);
+}
+
+void launch_update_oz(const Layout& L, void* work, int J, int num_sms, const CUtensorMap& mapA,
+                      const CUtensorMap& mapB, cudaStream_t s) {
     const int p0 = tile_start(L, J);
     if (p0 <= 0) return;
-    dim3 grid((p0 + BM - 1) / BM, (2 * L.ncolp) / BN);
-    k_update_oz<<<grid, 256, kSmem, s>>>(L, work, J);
+    // tiles per CTA: the fewest tile times for the busiest SM (one CTA per
+    // SM at a time; each CTA also pays about one tile time to load A_J)
+    const int mt = (p0 + TBM - 1) / TBM, nt = 2 * L.ncolp / TBN;
+    int per = nt;
+    long best = -1;
+    for (int c = 1; c <= nt; ++c) {
+        const long ctas = (long)mt * ((nt + c - 1) / c);
+        const long cost = (ctas + num_sms - 1) / num_sms * (c + 1);
+        if (best < 0 || cost < best) best = cost, per = c;
+    }
+    dim3 grid(mt, (nt + per - 1) / per);
+    k_update_oz<<<grid, kThreads, kSmem, s>>>(L, work, J, per, mapA, mapB);
 }
 
 cudaError_t update_oz_configure() {
