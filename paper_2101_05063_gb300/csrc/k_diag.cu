@@ -39,6 +39,8 @@
 #include "common.cuh"
 #include "ozaki.cuh"
 
+#include <type_traits>
+
 namespace hsein {
 namespace {
 
@@ -50,6 +52,15 @@ __device__ inline int lbound(double v) {
     const int ex = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
     if (ex != 0) return ex - 1022;
     return v == 0.0 ? kNegInfLog : ilogb(v) + 1;
+}
+
+// f(integral_constant<I>), f(integral_constant<I-1>), ..., f(integral_constant<0>)
+template <int I, class F>
+__device__ __forceinline__ void static_down(F&& f) {
+    if constexpr (I >= 0) {
+        f(std::integral_constant<int, I>{});
+        static_down<I - 1>(f);
+    }
 }
 
 template <int LPS>
@@ -86,7 +97,7 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
     double* Sv = ws<double>(work, L.off_S);
     double* ZW = ws<double>(work, L.off_ZW);
 
-    // per-group shared scratch: c (re, im), s, x (re, im)
+    // per-group shared scratch: c (re, im), s, x (re, im), shifted diagonal
     double* s_cr = sm;
     double* s_ci = sm + br;
     double* s_s = sm + 2 * br;
@@ -135,109 +146,202 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
     };
 
     // ---------------- phase 1: sweep k = bt-1 .. 1 -----------------------
+    // Step k forms the rotation of the pivot row k (lane k % LPS, slot
+    // k / LPS) lane-parallel: one FP64 multiply gives c, s and x(k)/phi in
+    // different lanes of the group and one more gives a and b, each followed
+    // by a shuffle, instead of every lane computing every scalar.  The rows
+    // above are then updated: the slot that holds row k-1 (the next pivot) at
+    // once, the slots below it one step later, in the same instruction stream
+    // as the next rotation, whose dependency chain would otherwise leave the
+    // FP64 pipe idle.  The unscaled, unprotected rotation is the fast path;
+    // when any group needs the overflow scaling of phi or a protection step
+    // (ProtectDivision / ProtectUpdate), the whole warp recomputes the step
+    // the careful way, which gives the same values whenever nothing rescales.
+    double* s_d = sm + 5 * br;  // h(i,i) - Re(lambda): the shifted diagonal
+    for (int i = r; i + 1 < bt; i += LPS) s_d[i] = Hs[(i + 1) * br + i] - lre;
+    __syncwarp();
+    const int role = r;
+    // the rotation waiting for the slots below the pivot slot (identity at first)
+    double p_ar = 0.0, p_ai = 0.0, p_bR = 0.0, p_bI = 0.0, p_cr = 0.0, p_ci = 0.0, p_s = 1.0;
+    const double* p_col = Hs;
+
+    auto apply_pending = [&](auto NPc) {
+        constexpr int NP = decltype(NPc)::value;
 #pragma unroll
-    for (int tk = RPL - 1; tk >= 0; --tk) {
-        for (int rk = LPS - 1; rk >= 0; --rk) {
-            const int k = LPS * tk + rk;
-            if (k >= bt || k == 0) continue;
-            const int src = gbase | rk;
-            double vkr = __shfl_sync(kFull, vr[tk], src);
-            double xkr = __shfl_sync(kFull, xr[tk], src);
-            double vki = 0.0, xki = 0.0;
+        for (int t = 0; t < NP; ++t) {
+            const double tr = p_col[r + LPS * t];
             if (CPLX) {
-                vki = __shfl_sync(kFull, vi[tk], src);
-                xki = __shfl_sync(kFull, xi[tk], src);
+                xr[t] = fma(-p_ar, vr[t], fma(p_ai, vi[t], fma(p_bR, tr, xr[t])));
+                xi[t] = fma(-p_ar, vi[t], fma(-p_ai, vr[t], fma(p_bI, tr, xi[t])));
+                const double nvr = fma(p_cr, tr, p_s * vr[t]);
+                const double nvi = fma(p_ci, tr, p_s * vi[t]);
+                vr[t] = nvr;
+                vi[t] = nvi;
+            } else {
+                xr[t] = fma(-p_ar, vr[t], fma(p_bR, tr, xr[t]));
+                vr[t] = fma(p_cr, tr, p_s * vr[t]);
             }
-            // rotation: 1/phi = rsqrt(h^2 + |v|^2), guarded against overflow
-            double hs = Hs[k * br + k], vsr = vkr, vsi = vki, sc = 1.0;
-            int eh = max(lbound(hs), lbound(vsr));
-            if (CPLX) eh = max(eh, lbound(vsi));
+        }
+    };
+
+    // one step; TK = slot of the pivot row k, PEEL = the step with k % LPS == 0
+    // (row k-1 then sits in slot TK-1)
+    auto step = [&](auto TKc, auto PEELc, int rk) {
+        constexpr int TK = decltype(TKc)::value;
+        constexpr bool PEEL = decltype(PEELc)::value;
+        constexpr int US = PEEL ? TK - 1 : TK;  // slot of row k-1
+        const int k = LPS * TK + rk;
+        const int src = gbase | rk;
+        const double vkr = __shfl_sync(kFull, vr[TK], src);
+        const double xkr = __shfl_sync(kFull, xr[TK], src);
+        const double vki = CPLX ? __shfl_sync(kFull, vi[TK], src) : 0.0;
+        const double xki = CPLX ? __shfl_sync(kFull, xi[TK], src) : 0.0;
+        const double* Hcol = Hs + (size_t)k * br;  // h(:, k-1) of the tile
+        const double hs = Hcol[k];                 // h(k, k-1)
+        apply_pending(std::integral_constant<int, TK>{});
+
+        // rotation (eq. "givens" / "cgivens"): 1/phi = rsqrt(h^2 + |v|^2)
+        const double ss = CPLX ? fma(vkr, vkr, fma(vki, vki, hs * hs)) : fma(vkr, vkr, hs * hs);
+        const double rr = rsqrt(ss);
+        double m1;
+        if (CPLX)
+            m1 = role == 0 ? vkr : role == 1 ? vki : role == 2 ? -hs : role == 3 ? xkr : xki;
+        else
+            m1 = role == 0 ? vkr : role == 1 ? -hs : xkr;
+        const double f1 = m1 * rr;
+        double cr = __shfl_sync(kFull, f1, gbase);
+        double ci = CPLX ? __shfl_sync(kFull, f1, gbase | 1) : 0.0;
+        double s = __shfl_sync(kFull, f1, gbase | (CPLX ? 2 : 1));
+        double xkr1 = __shfl_sync(kFull, f1, gbase | (CPLX ? 3 : 2));
+        double xki1 = CPLX ? __shfl_sync(kFull, f1, gbase | 4) : 0.0;
+        // a = x(k) conj(c), b = x(k) s
+        double f2;
+        if (CPLX) {
+            const double u0 = (role & 1) ? xki1 : xkr1;
+            const double v0 = role < 2 ? cr : s;
+            const double u1 = role == 0 ? xki1 : role == 1 ? -xkr1 : 0.0;
+            const double v1 = role < 2 ? ci : 0.0;
+            f2 = fma(u0, v0, u1 * v1);
+        } else {
+            f2 = xkr1 * (role == 0 ? cr : s);
+        }
+        double ar = __shfl_sync(kFull, f2, gbase);
+        double ai = CPLX ? __shfl_sync(kFull, f2, gbase | 1) : 0.0;
+        double bR = __shfl_sync(kFull, f2, gbase | (CPLX ? 2 : 1));
+        double bI = CPLX ? __shfl_sync(kFull, f2, gbase | 3) : 0.0;
+
+        int eh = max(lbound(hs), lbound(vkr));
+        if (CPLX) eh = max(eh, lbound(vki));
+        bool need = eh > 500 || eh < -500;
+        int nb = 0;
+        if (robust) {
+            const int sq = lb2(xkr, xki) + lbound(rr) - om;  // ProtectDivision
+            nb = max(bx, LRb + lb2(xkr1, xki1)) + 1;          // ProtectUpdate
+            need = need || sq > 0 || nb > om;
+        }
+        if (__any_sync(kFull, need)) {
+            // careful step: phi with a power-of-two prescale against
+            // overflow, then the protections with rescaling of x
+            double hsc = hs, vsr = vkr, vsi = vki, sc = 1.0;
             if (eh > 500 || eh < -500) {
                 sc = scalbn(1.0, -eh);
-                hs *= sc;
+                hsc *= sc;
                 vsr *= sc;
                 if (CPLX) vsi *= sc;
             }
-            const double ss = CPLX ? fma(vsr, vsr, fma(vsi, vsi, hs * hs)) : fma(vsr, vsr, hs * hs);
-            const double rr = rsqrt(ss);
-            const double cr = vsr * rr, s = -hs * rr;
-            const double ci = CPLX ? vsi * rr : 0.0;
-            const double rinv = rr * sc;
-            if (robust) {  // ProtectDivision: |x(k)| / phi < 2^om
-                const int sq = lb2(xkr, xki) + lbound(rinv) - om;
-                if (sq > 0) rescale(sq, xkr, xki);
+            const double ss2 =
+                CPLX ? fma(vsr, vsr, fma(vsi, vsi, hsc * hsc)) : fma(vsr, vsr, hsc * hsc);
+            const double rr2 = rsqrt(ss2);
+            cr = vsr * rr2;
+            s = -hsc * rr2;
+            ci = CPLX ? vsi * rr2 : 0.0;
+            const double rinv = rr2 * sc;
+            xkr1 = xkr;
+            xki1 = xki;
+            if (robust) {
+                const int sq = lb2(xkr1, xki1) + lbound(rinv) - om;
+                if (sq > 0) rescale(sq, xkr1, xki1);
             }
-            xkr *= rinv;
-            if (CPLX) xki *= rinv;
-            if (robust) {  // ProtectUpdate: |x| + |R| |x(k)| < 2^om
-                const int lx = lb2(xkr, xki);
-                int nb = max(bx, LRb + lx) + 1;
-                const bool refine = nb > om;
+            xkr1 *= rinv;
+            if (CPLX) xki1 *= rinv;
+            if (robust) {
+                const int lx = lb2(xkr1, xki1);
+                int nb2 = max(bx, LRb + lx) + 1;
+                const bool refine = nb2 > om;
                 // the exact maximum is a shuffle over the group: every lane of
                 // the warp takes part whenever any group needs it
                 if (__any_sync(kFull, refine)) {
                     const int bexact = xmax_bound();
                     if (refine) {
                         bx = max(bexact, lx);
-                        nb = max(bx, LRb + lx) + 1;
-                        if (nb > om) {
-                            rescale(nb - om, xkr, xki);
-                            nb = om;
+                        nb2 = max(bx, LRb + lx) + 1;
+                        if (nb2 > om) {
+                            rescale(nb2 - om, xkr1, xki1);
+                            nb2 = om;
                         }
                     }
                 }
-                bx = nb;
+                bx = nb2;
             }
-            // a = x(k) conj(c), b = x(k) s
-            const double ar = CPLX ? fma(xkr, cr, xki * ci) : xkr * cr;
-            const double ai = CPLX ? fma(xki, cr, -xkr * ci) : 0.0;
-            const double bR = xkr * s;
-            const double bI = CPLX ? xki * s : 0.0;
-#pragma unroll
-            for (int t = 0; t <= tk; ++t) {
-                if (t < tk || r < rk) {
-                    const double tr = Hs[k * br + r + LPS * t];
-                    if (CPLX) {
-                        // x -= a v - b t
-                        xr[t] = fma(-ar, vr[t], fma(ai, vi[t], fma(bR, tr, xr[t])));
-                        xi[t] = fma(-ar, vi[t], fma(-ai, vr[t], fma(bI, tr, xi[t])));
-                        const double nvr = fma(cr, tr, s * vr[t]);
-                        const double nvi = fma(ci, tr, s * vi[t]);
-                        vr[t] = nvr;
-                        vi[t] = nvi;
-                    } else {
-                        xr[t] = fma(-ar, vr[t], fma(bR, tr, xr[t]));
-                        vr[t] = fma(cr, tr, s * vr[t]);
-                    }
-                }
-            }
-            // the shift on the diagonal entry of column k-1 (row k-1):
-            // x -= b lambda, v -= c lambda
-            auto diag_fix = [&](double& xa, double& xb, double& va, double& vb) {
+            ar = CPLX ? fma(xkr1, cr, xki1 * ci) : xkr1 * cr;
+            ai = CPLX ? fma(xki1, cr, -xkr1 * ci) : 0.0;
+            bR = xkr1 * s;
+            bI = CPLX ? xki1 * s : 0.0;
+        } else if (robust) {
+            bx = nb;
+        }
+
+        // row k is final
+        if (r == rk) {
+            xr[TK] = xkr1;
+            if (CPLX) xi[TK] = xki1;
+            s_cr[k] = cr;
+            if (CPLX) s_ci[k] = ci;
+            s_s[k] = s;
+        }
+        // slot US now (it holds row k-1, whose t entry is the shifted
+        // diagonal h(k-1,k-1) - lambda): x -= a v - b t, v = c t + s v
+        {
+            const int i = r + LPS * US;
+            const bool dg = i == k - 1;
+            if (PEEL || r < rk) {
+                const double tr = dg ? s_d[i] : Hcol[i];
                 if (CPLX) {
-                    xa = fma(-bR, lre, fma(bI, lim, xa));
-                    xb = fma(-bR, lim, fma(-bI, lre, xb));
-                    va = fma(-cr, lre, fma(ci, lim, va));
-                    vb = fma(-cr, lim, fma(-ci, lre, vb));
+                    const double dli = dg ? lim : 0.0;  // t = tr - i lim on the diagonal
+                    xr[US] = fma(bI, dli, fma(-ar, vr[US], fma(ai, vi[US], fma(bR, tr, xr[US]))));
+                    xi[US] = fma(-bR, dli, fma(-ar, vi[US], fma(-ai, vr[US], fma(bI, tr, xi[US]))));
+                    const double nvr = fma(ci, dli, fma(cr, tr, s * vr[US]));
+                    const double nvi = fma(-cr, dli, fma(ci, tr, s * vi[US]));
+                    vr[US] = nvr;
+                    vi[US] = nvi;
                 } else {
-                    xa = fma(-bR, lre, xa);
-                    va = fma(-cr, lre, va);
+                    xr[US] = fma(-ar, vr[US], fma(bR, tr, xr[US]));
+                    vr[US] = fma(cr, tr, s * vr[US]);
                 }
-            };
-            if (rk > 0) {
-                if (r == rk - 1) diag_fix(xr[tk], xi[tk], vr[tk], vi[tk]);
-            } else if (tk > 0) {
-                if (r == LPS - 1) diag_fix(xr[tk - 1], xi[tk - 1], vr[tk - 1], vi[tk - 1]);
-            }
-            if (r == rk) {
-                xr[tk] = xkr;
-                if (CPLX) xi[tk] = xki;
-                s_cr[k] = cr;
-                if (CPLX) s_ci[k] = ci;
-                s_s[k] = s;
             }
         }
-    }
+        // the slots below US take this rotation at the next step
+        p_ar = ar;
+        p_ai = ai;
+        p_bR = bR;
+        p_bI = bI;
+        p_cr = cr;
+        p_ci = ci;
+        p_s = s;
+        p_col = Hcol;
+    };
+
+    auto block = [&](auto TKc) {
+        constexpr int TK = decltype(TKc)::value;
+        for (int rk = LPS - 1; rk >= 1; --rk) {
+            if (LPS * TK + rk >= bt) continue;
+            step(TKc, std::false_type{}, rk);
+        }
+        if constexpr (TK >= 1) {
+            if (LPS * TK < bt) step(TKc, std::true_type{}, 0);
+        }
+    };
+    static_down<RPL - 1>(block);
 
     // ---------------- row 0: left rotation or final pivot ----------------
     {
@@ -555,13 +659,13 @@ k_diag(Layout L, void* work, int J, int robust, int om, int nbc) {
         constexpr int G = 32 / LPSC;
         const int g = lane / LPSC;
         const int q = G * b + g;
-        double* scratch = smem + (size_t)br * br + (size_t)g * 5 * br;
+        double* scratch = smem + (size_t)br * br + (size_t)g * 6 * br;
         tile_group<LPSC, RPLC, true>(L, work, Hs, J, p0, bt, q, q < L.mc, robust, om, scratch);
     } else {
         constexpr int G = 32 / LPSR;
         const int g = lane / LPSR;
         const int q = L.mc + G * (b - nbc) + g;
-        double* scratch = smem + (size_t)br * br + (size_t)g * 5 * br;
+        double* scratch = smem + (size_t)br * br + (size_t)g * 6 * br;
         tile_group<LPSR, RPLR, false>(L, work, Hs, J, p0, bt, q, q < L.m, robust, om, scratch);
     }
 }
@@ -611,7 +715,7 @@ static void launch_t(const Layout& L, void* work, int J, int robust, int om, int
 }
 
 static size_t diag_smem(int br) {
-    return ((size_t)br * br + (size_t)kMaxGroups * 5 * br) * sizeof(double);
+    return ((size_t)br * br + (size_t)kMaxGroups * 6 * br) * sizeof(double);
 }
 
 void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, int robust,
