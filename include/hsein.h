@@ -79,8 +79,9 @@ hsein_status hsein_default_options(hsein_options *opt);
 /*
  * Create a plan for n x n matrices and m_real real plus m_cplx complex shifts
  * (ncol = m_real + 2 m_cplx solution columns).  opt may be NULL (defaults).
- * *workspace_bytes receives the device workspace size hsein_solve and
- * hsein_backtransform need.  n >= 1, m_real >= 0, m_cplx >= 0,
+ * *workspace_bytes receives the device workspace size hsein_solve,
+ * hsein_backtransform and hsein_restart need (the last one needs a few times
+ * 8n bytes beyond what the solve itself uses).  n >= 1, m_real >= 0, m_cplx >= 0,
  * m_real + m_cplx >= 1.  On error *plan is set to NULL.
  */
 hsein_status hsein_plan(hsein_plan_t *plan, int n, int m_real, int m_cplx,
@@ -146,6 +147,44 @@ hsein_status hsein_solve_noalloc(hsein_plan_t plan, const double *dH, int ldh,
 hsein_status hsein_backtransform(hsein_plan_t plan, const double *dQ0, int ldq,
                                  const double *dX, int ldx, double *dZ, int ldz,
                                  void *dWork, size_t work_bytes, void *stream);
+
+/*
+ * Restart loop of inverse iteration (Alg. "hsrq3in", Sec. 4.2).  Call after
+ * hsein_solve with the same arguments: every shift whose status is
+ * HSEIN_COL_NOT_CONVERGED is solved again, up to max_tries times, from a new
+ * starting vector orthogonal to the previous choices (the given column of dB,
+ * or rho*e, and the earlier trials): trial t is column n+1-t of the
+ * Householder reflector whose first column is b/||b|| (real shift), or of the
+ * Householder QR factor of [Re b, Im b] (complex shift; a real vector, so
+ * b^H x = 0).  Converged results replace the zeroed columns of dX and their
+ * status becomes HSEIN_COL_OK; the others keep HSEIN_COL_NOT_CONVERGED.
+ *   max_tries >= 0 (at most n-2 are used); *n_retried (may be NULL) = the
+ *   number of shifts that were retried.
+ *   dWork / work_bytes as for hsein_solve; the restart uses it for
+ *   sub-problems of the retried shifts (chunked when they do not fit), so
+ *   hsein_margins and hsein_plan_sync_status afterwards describe the last
+ *   sub-problem, not the original solve.
+ * Synchronizes `stream` (which shifts to retry is decided on the host).
+ * Returns HSEIN_OK when every shift has converged, HSEIN_WNOTCONVERGED if
+ * some have not, HSEIN_ECUDA on a CUDA or device error, HSEIN_ENOMEM if not
+ * even one retried shift fits in dWork.
+ */
+hsein_status hsein_restart(hsein_plan_t plan, const double *dH, int ldh,
+                           const double *dWr, const double *dWi,
+                           const double *dB, int ldb, double *dX, int ldx,
+                           int *dStatus, int max_tries, int *n_retried,
+                           void *dWork, size_t work_bytes, void *stream);
+
+/*
+ * Convergence margins of the last hsein_solve that used dWork: for every
+ * shift, in input order, log2(||x||_2 / ||b||_2) - log2(1 / (10 n ||H||_inf
+ * eps)), the amount (in powers of two) by which one step of inverse
+ * iteration exceeded Varah's threshold (Sec. 4.2); > 0 means converged,
+ * -HUGE_VAL a zero solution.  Copies m doubles to the device array dMargin,
+ * stream-ordered.  The paper has no counterpart: a diagnostic of how close a
+ * column came to the test.
+ */
+hsein_status hsein_margins(hsein_plan_t plan, const void *dWork, double *dMargin, void *stream);
 
 /*
  * Wait for `stream`, then return the device-side status of the last

@@ -189,3 +189,42 @@ def gehrd(A):
     work = np.empty(2 * n)
     _load().oracle_gehrd(n, _dp(A), n, _dp(H), n, _dp(Q), n, _dp(work))
     return H, Q
+
+
+def restart_vector(b, t, b_im=None):
+    """Trial starting vector t (t = 1, 2, ...) for a shift whose solve from
+    the starting vector b (real; with b_im the complex vector b + i b_im) did
+    not converge: the restart of Alg. "hsrq3in" (Sec. 4.2) asks for a new
+    start orthogonal to the previous choices.  Reading used here: the
+    Householder QR of [b] (real) or [Re b, Im b] (complex) gives an orthogonal
+    Q whose leading columns span the previous start; trial t is column
+    n+1-t of Q (a real unit vector, orthogonal to b and to the other trials).
+    Each reflector is I - 2 w w^T / (w^T w), w = a/||a|| + sign(a_1) e_1, with
+    the second reflector acting on rows 2..n; it is skipped when the
+    imaginary part lies in the span of the real part (the part outside it is
+    below 2^-50 of the whole).  With Re b = 0 the imaginary part leads; with
+    b = 0 trial t is e_(n+1-t).  Plain numpy, test infrastructure only."""
+    a1 = np.array(b, dtype=np.float64)
+    n = a1.shape[0]
+    a2 = None if b_im is None else np.array(b_im, dtype=np.float64)
+    if a2 is not None and not np.any(a1):
+        a1, a2 = a2, a1
+    j = n - t  # 0-based column of Q
+    y = np.zeros(n)
+    y[j] = 1.0
+    if not np.any(a1):
+        return y
+
+    def reflector(a):
+        v = a / np.linalg.norm(a)
+        w = v.copy()
+        w[0] += 1.0 if v[0] >= 0.0 else -1.0
+        return w
+
+    w1 = reflector(a1)
+    if a2 is not None:
+        u = a2 - 2.0 * (w1 @ a2) / (w1 @ w1) * w1  # P1 a2
+        if np.abs(u[1:]).max() > 2.0 ** -50 * np.abs(u).max():
+            w2 = reflector(u[1:])
+            y[1:] = y[1:] - 2.0 * (w2 @ y[1:]) / (w2 @ w2) * w2  # P2 e_j
+    return y - 2.0 * (w1 @ y) / (w1 @ w1) * w1  # P1 y

@@ -21,7 +21,9 @@ from . import build as _build
 
 __all__ = [
     "HseinError", "HseinOptions", "load", "hsein_default_options", "hsein_plan", "hsein_solve",
-    "hsein_solve_noalloc", "hsein_backtransform", "hsein_plan_sync_status", "hsein_plan_info", "hsein_plan_destroy",
+    "hsein_solve_noalloc", "hsein_backtransform", "hsein_plan_sync_status", "hsein_margins",
+    "hsein_restart",
+    "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
     "STATUS", "PHASES",
 ]
@@ -73,6 +75,11 @@ def load(build_if_missing=True):
     lib.hsein_backtransform.argtypes = [vp, dp, ip, dp, ip, dp, ip, vp, sz, vp]
     lib.hsein_plan_sync_status.restype = ctypes.c_int
     lib.hsein_plan_sync_status.argtypes = [vp, vp, vp]
+    lib.hsein_margins.restype = ctypes.c_int
+    lib.hsein_margins.argtypes = [vp, vp, dp, vp]
+    lib.hsein_restart.restype = ctypes.c_int
+    lib.hsein_restart.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, ip,
+                                  ctypes.POINTER(ctypes.c_int), vp, sz, vp]
     lib.hsein_plan_info.restype = ctypes.c_int
     lib.hsein_plan_info.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5 + [ctypes.POINTER(sz)]
     lib.hsein_plan_destroy.restype = ctypes.c_int
@@ -126,6 +133,21 @@ def hsein_backtransform(plan, dQ0, ldq, dX, ldx, dZ, ldz, dWork, work_bytes, str
 
 def hsein_plan_sync_status(plan, dWork, stream):
     return load().hsein_plan_sync_status(plan, dWork, stream or None)
+
+
+def hsein_margins(plan, dWork, dMargin, stream):
+    """Per-shift Varah margins (log2, > 0 converged) of the last solve on dWork."""
+    return load().hsein_margins(plan, dWork, dMargin, stream or None)
+
+
+def hsein_restart(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, max_tries, dWork,
+                  work_bytes, stream):
+    """Retry the non-converged shifts with new orthogonal starting vectors;
+    returns (status code, number of shifts retried)."""
+    k = ctypes.c_int(0)
+    rc = load().hsein_restart(plan, dH, ldh, dWr, dWi, dB or None, ldb, dX, ldx, dStatus,
+                              int(max_tries), ctypes.byref(k), dWork, work_bytes, stream or None)
+    return rc, k.value
 
 
 def hsein_plan_info(plan):
@@ -245,6 +267,34 @@ class Solver:
 
     def device_status(self):
         return hsein_plan_sync_status(self.plan, self.work.data_ptr(), self._stream())
+
+    def restart(self, H, wr, wi, X, status, B=None, max_tries=3):
+        """Alg. "hsrq3in": retry the shifts whose status is 1 from new starting
+        vectors orthogonal to the previous ones, in place in X and status.
+        Synchronizes the stream; returns (code, shifts retried), code 0 when
+        every shift converged, 1 (HSEIN_WNOTCONVERGED) otherwise."""
+        torch = self.torch
+        H = _colmajor(H, torch)
+        wr = wr.to(torch.float64).contiguous()
+        wi = wi.to(torch.float64).contiguous()
+        if B is not None:
+            B = _colmajor(B, torch)
+        rc, k = hsein_restart(self.plan, H.data_ptr(), _ld(H), wr.data_ptr(), wi.data_ptr(),
+                              B.data_ptr() if B is not None else 0,
+                              _ld(B) if B is not None else self.n, X.data_ptr(), _ld(X),
+                              status.data_ptr(), int(max_tries), self.work.data_ptr(),
+                              self.work_bytes, self._stream())
+        if rc < 0:
+            _check(rc, "hsein_restart")
+        return rc, k
+
+    def margins(self):
+        """Varah margins of the last solve, per shift in input order (log2;
+        > 0 converged)."""
+        out = self.torch.empty(self.m, dtype=self.torch.float64, device=self.device)
+        _check(hsein_margins(self.plan, self.work.data_ptr(), out.data_ptr(), self._stream()),
+               "hsein_margins")
+        return out
 
     def backtransform(self, Q0, X, Z=None):
         """Z = Q0 X (eigenvectors of A = Q0 H Q0^T)."""

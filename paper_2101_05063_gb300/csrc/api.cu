@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "ozaki.cuh"
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <new>
@@ -86,6 +87,7 @@ void make_layout(Layout* L, int n, int mr, int mc, int br, int precision) {
     L->off_S = take(sizeof(double) * nn * m);
     L->off_ZW = take(sizeof(double) * (size_t)br * 2 * L->ncolp);
     L->off_dt = take(sizeof(double) * N * br * br);
+    L->off_margin = take(sizeof(double) * m);
     L->oz = precision == 1 ? 1 : 0;
     {
         const size_t P = L->oz ? hsein::oz_update_hd_elems(*L) : 0;
@@ -102,6 +104,14 @@ void make_layout(Layout* L, int n, int mr, int mc, int br, int precision) {
 }
 
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
+
+// room for one retried shift of hsein_restart (map, shift, status, two
+// starting-vector and two solution columns, trial scratch) beside the
+// sub-problem's own workspace, which is never larger than the plan's
+size_t restart_reserve(int n) {
+    return 8 * 256 + 4 * align256(sizeof(double) * 2 * (size_t)n) +
+           align256(hsein::restart_scratch_bytes(n, 1));
+}
 
 cudaEvent_t next_event(hsein_plan_s* p) {
     if (p->used == p->pool.size()) {
@@ -176,7 +186,7 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         delete p;
         return HSEIN_ECUDA;
     }
-    if (workspace_bytes) *workspace_bytes = p->L.total;
+    if (workspace_bytes) *workspace_bytes = p->L.total + restart_reserve(n);
     *plan = p;
     return HSEIN_OK;
 }
@@ -189,7 +199,7 @@ hsein_status hsein_plan_info(hsein_plan_t plan, int* n, int* m_real, int* m_cplx
     if (m_cplx) *m_cplx = plan->L.mc;
     if (ncol) *ncol = plan->L.ncol;
     if (br) *br = plan->L.br;
-    if (workspace_bytes) *workspace_bytes = plan->L.total;
+    if (workspace_bytes) *workspace_bytes = plan->L.total + restart_reserve(plan->L.n);
     return HSEIN_OK;
 }
 
@@ -265,6 +275,134 @@ hsein_status hsein_backtransform(hsein_plan_t plan, const double* dQ0, int ldq, 
         hsein::launch_q0(L, dQ0, ldq, dX, ldx, dZ, ldz, s);
     }
     if (cudaGetLastError() != cudaSuccess) return HSEIN_ECUDA;
+    return HSEIN_OK;
+}
+
+// Restart loop of Alg. "hsrq3in": the host reads the status array, then for
+// trial t = 1, 2, ... solves the shifts that are still not converged again
+// from the trial starting vectors of csrc/restart.cu, as a sub-problem with
+// its own (host-only) plan whose workspace, shifts, starting vectors and
+// results are carved out of dWork.
+hsein_status hsein_restart(hsein_plan_t plan, const double* dH, int ldh, const double* dWr,
+                           const double* dWi, const double* dB, int ldb, double* dX, int ldx,
+                           int* dStatus, int max_tries, int* n_retried, void* dWork,
+                           size_t work_bytes, void* stream) {
+    if (!plan) return HSEIN_EARG;
+    const Layout& L = plan->L;
+    if (!dH || ldh < L.n || !dWr || !dWi || !dX || ldx < L.n || !dStatus || max_tries < 0)
+        return HSEIN_EARG;
+    if (dB && ldb < L.n) return HSEIN_EARG;
+    if (!dWork || !aligned256(dWork)) return HSEIN_EARG;
+    if (work_bytes < L.total + restart_reserve(L.n)) return HSEIN_ENOMEM;
+    if (n_retried) *n_retried = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = L.n, m = L.m;
+    std::vector<int> st(m);
+    std::vector<double> wi(m);
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpy(st.data(), dStatus, sizeof(int) * m, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(wi.data(), dWi, sizeof(double) * m, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HSEIN_ECUDA;
+    std::vector<int> ucol(m), failed;
+    for (int l = 0, c = 0; l < m; ++l) {
+        ucol[l] = c;
+        c += wi[l] != 0.0 ? 2 : 1;
+        if (st[l] == HSEIN_COL_INVALID) return HSEIN_ECUDA;
+        if (st[l] == HSEIN_COL_NOT_CONVERGED) failed.push_back(l);
+    }
+    if (n_retried) *n_retried = (int)failed.size();
+    // trial columns n+1-t of the orthogonal factors: t <= n-2 (complex), n-1 (real)
+    const int tmax = std::min(max_tries, n - 2);
+    for (int t = 1; t <= tmax && !failed.empty(); ++t) {
+        std::vector<int> still;
+        size_t pos = 0;
+        while (pos < failed.size()) {
+            // the largest chunk whose sub-problem and buffers fit in dWork
+            int k = (int)(failed.size() - pos);
+            hsein_plan_t sub = nullptr;
+            size_t subw = 0, off_map = 0, off_wr = 0, off_wi = 0, off_st = 0, off_b = 0,
+                   off_x = 0, off_sc = 0, end = 0;
+            for (;;) {
+                int kr = 0, kc = 0;
+                for (int j = 0; j < k; ++j) (wi[failed[pos + j]] != 0.0 ? kc : kr)++;
+                const size_t ncs = (size_t)kr + 2 * (size_t)kc;
+                const hsein_status rc = hsein_plan(&sub, n, kr, kc, &plan->opt, nullptr);
+                if (rc != HSEIN_OK) return rc;
+                subw = sub->L.total;  // what the sub-solve needs (no restart reserve)
+                size_t o = align256(subw);
+                auto take = [&](size_t b) {
+                    size_t at = o;
+                    o = align256(o + b);
+                    return at;
+                };
+                off_map = take(sizeof(int) * 4 * (size_t)k);
+                off_wr = take(sizeof(double) * k);
+                off_wi = take(sizeof(double) * k);
+                off_st = take(sizeof(int) * k);
+                off_b = take(sizeof(double) * (size_t)n * ncs);
+                off_x = take(sizeof(double) * (size_t)n * ncs);
+                off_sc = take(hsein::restart_scratch_bytes(n, k));
+                end = o;
+                if (end <= work_bytes) break;
+                hsein_plan_destroy(sub);
+                sub = nullptr;
+                if (k == 1) return HSEIN_ENOMEM;
+                k = (k + 1) / 2;
+            }
+            char* w = static_cast<char*>(dWork);
+            std::vector<int> map(4 * (size_t)k);
+            for (int j = 0, us = 0; j < k; ++j) {
+                const int l = failed[pos + j];
+                const int cp = wi[l] != 0.0 ? 1 : 0;
+                map[4 * j] = l;
+                map[4 * j + 1] = ucol[l];
+                map[4 * j + 2] = us;
+                map[4 * j + 3] = cp;
+                us += cp ? 2 : 1;
+            }
+            int* dmap = reinterpret_cast<int*>(w + off_map);
+            double* wr_s = reinterpret_cast<double*>(w + off_wr);
+            double* wi_s = reinterpret_cast<double*>(w + off_wi);
+            int* st_s = reinterpret_cast<int*>(w + off_st);
+            double* Bs = reinterpret_cast<double*>(w + off_b);
+            double* Xs = reinterpret_cast<double*>(w + off_x);
+            double* scr = reinterpret_cast<double*>(w + off_sc);
+            hsein_status rc = HSEIN_OK;
+            if (cudaMemcpy(dmap, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+                rc = HSEIN_ECUDA;
+            if (rc == HSEIN_OK) {
+                hsein::launch_restart_trial(n, t, k, dmap, dWr, dWi, dB, ldb, wr_s, wi_s, Bs, scr, s);
+                rc = hsein_solve(sub, dH, ldh, wr_s, wi_s, Bs, n, Xs, n, st_s, dWork, subw, stream);
+            }
+            if (rc == HSEIN_OK) {
+                hsein::launch_restart_scatter(n, k, dmap, Xs, st_s, dX, ldx, dStatus, s);
+                std::vector<int> sts(k);
+                if (cudaMemcpyAsync(sts.data(), st_s, sizeof(int) * k, cudaMemcpyDeviceToHost, s) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    rc = HSEIN_ECUDA;
+                for (int j = 0; j < k && rc == HSEIN_OK; ++j) {
+                    if (sts[j] == HSEIN_COL_INVALID) rc = HSEIN_ECUDA;
+                    else if (sts[j] != HSEIN_COL_OK) still.push_back(failed[pos + j]);
+                }
+            }
+            hsein_plan_destroy(sub);
+            if (rc != HSEIN_OK) return rc;
+            pos += k;
+        }
+        failed.swap(still);
+    }
+    if (cudaGetLastError() != cudaSuccess) return HSEIN_ECUDA;
+    return failed.empty() ? HSEIN_OK : HSEIN_WNOTCONVERGED;
+}
+
+hsein_status hsein_margins(hsein_plan_t plan, const void* dWork, double* dMargin, void* stream) {
+    if (!plan || !dWork || !dMargin) return HSEIN_EARG;
+    const char* src = static_cast<const char*>(dWork) + plan->L.off_margin;
+    if (cudaMemcpyAsync(dMargin, src, sizeof(double) * plan->L.m, cudaMemcpyDeviceToDevice,
+                        static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return HSEIN_ECUDA;
     return HSEIN_OK;
 }
 

@@ -62,7 +62,7 @@ struct Layout {
     int n, m, mr, mc, ncol, ncolp, br, N, b0, ldw;
     size_t off_state, off_qsrc, off_qcol, off_lam, off_bnorm, off_eB, off_etile, off_bmax,
         off_rmax, off_epi, off_anorm, off_rowpart, off_X, off_R, off_Cr, off_Ci, off_S, off_ZW,
-        off_dt, off_hd, off_he, off_zwd, off_zwf, off_oz, total;
+        off_dt, off_hd, off_he, off_zwd, off_zwf, off_margin, off_oz, total;
     int oz;  // 1: split-precision shared-H update (BF16 digits), 0: FP64
 };
 
@@ -118,6 +118,13 @@ void launch_split_h(const Layout& L, void* work, const double* H, int ldh, cudaS
 size_t oz_update_hd_elems(const Layout& L);
 void launch_finalize(const Layout& L, void* work, double* X, int ldx, int* status,
                      cudaStream_t s);
+// restart of non-converged shifts (csrc/restart.cu)
+size_t restart_scratch_bytes(int n, int k);
+void launch_restart_trial(int n, int t, int k, const int* map, const double* wr, const double* wi,
+                          const double* B, int ldb, double* wr_s, double* wi_s, double* Bs,
+                          double* scratch, cudaStream_t s);
+void launch_restart_scatter(int n, int k, const int* map, const double* Xs, const int* st_s,
+                            double* X, int ldx, int* status, cudaStream_t s);
 void launch_q0(const Layout& L, const double* Q, int ldq, const double* X, int ldx, double* Z,
                int ldz, cudaStream_t s);
 

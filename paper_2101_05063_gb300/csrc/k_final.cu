@@ -119,7 +119,9 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
         for (int w = 0; w < kThreads / 32; ++w) a = nrm_merge(a, Nrm{s_m[w], s_t[w]});
         const double nrm = a.m * sqrt(a.t);
         const double thr = -log2(10.0 * n * st->hnorm * 0x1p-53);
-        int conv = (nrm > 0.0) && (log2(nrm) + emax - log2(bnorm[q]) > thr);
+        const double margin = nrm > 0.0 ? log2(nrm) + emax - log2(bnorm[q]) - thr : -HUGE_VAL;
+        int conv = margin > 0.0;
+        ws<double>(work, L.off_margin)[qsrc[q]] = margin;
         s_conv = conv;
         s_scale = conv ? 1.0 / nrm : 0.0;
     }

@@ -365,3 +365,52 @@ def test_bad_system_h2_through_the_driver():
     assert status[0] == 0 and exps[0] > 900
     assert np.all(np.isfinite(X)) and abs(np.linalg.norm(X[:, 0]) - 1.0) <= 4 * n * EPS
     assert residual(H, 2.0, X[:, 0]) <= 100 * n * EPS
+
+
+# ---------------------------------------------------------------- restart
+# Alg. "hsrq3in" (Sec. 4.2): a new starting vector orthogonal to the previous
+# choices.  Pins: closed forms at n = 2 (real) and n = 3 (complex: the
+# normalized cross product of Re b and Im b), and orthonormality of the
+# trials and their orthogonality to the previous start at larger n.
+
+def test_restart_vector_closed_form_real_n2():
+    b = np.array([3.0, -4.0])
+    y = oracle.restart_vector(b, 1)
+    expect = np.array([4.0, 3.0]) / 5.0  # the unit vector orthogonal to b
+    assert min(np.abs(y - expect).max(), np.abs(y + expect).max()) <= 1e-15
+
+
+def test_restart_vector_closed_form_complex_n3():
+    br = np.array([1.0, 2.0, -1.0])
+    bi = np.array([0.5, -1.0, 3.0])
+    y = oracle.restart_vector(br, 1, bi)
+    c = np.cross(br, bi)
+    c /= np.linalg.norm(c)
+    assert min(np.abs(y - c).max(), np.abs(y + c).max()) <= 1e-14
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_restart_vectors_orthonormal_and_orthogonal_to_start(cplx):
+    n = 40
+    br = hi.normal(71, 1, n)
+    bi = hi.normal(72, 1, n) if cplx else None
+    T = 6
+    Y = np.stack([oracle.restart_vector(br, t, bi) for t in range(1, T + 1)], axis=1)
+    assert np.abs(Y.T @ Y - np.eye(T)).max() <= 1e-14
+    assert np.abs(br @ Y).max() <= 1e-13 * np.linalg.norm(br)
+    if cplx:
+        assert np.abs(bi @ Y).max() <= 1e-13 * np.linalg.norm(bi)
+
+
+def test_restart_vector_degenerate_starts():
+    n = 8
+    # imaginary part in the span of the real part: only the real part counts
+    br = np.arange(1.0, n + 1)
+    y = oracle.restart_vector(br, 2, 3.0 * br)
+    assert abs(br @ y) <= 1e-13 * np.linalg.norm(br) and abs(np.linalg.norm(y) - 1) <= 1e-15
+    # zero real part: the imaginary part leads
+    y = oracle.restart_vector(np.zeros(n), 1, br)
+    assert abs(br @ y) <= 1e-13 * np.linalg.norm(br)
+    # zero start: a unit basis vector
+    y = oracle.restart_vector(np.zeros(n), 3)
+    assert y[n - 3] == 1.0 and np.abs(y).sum() == 1.0
