@@ -31,6 +31,9 @@ from .configs import (
     config0,
     config1,
     config2,
+    config3,
+    config3_sizes,
+    batch_instance,
     small_instance,
     column_offsets,
 )
@@ -38,6 +41,6 @@ from .configs import (
 __all__ = [
     "splitmix64", "uniform", "normal", "haar_orthogonal", "quasi_triangular",
     "hessenberg_reduce", "paper_h2", "paper_h3", "paper_r2_q2", "companion", "graded",
-    "unit_columns", "Instance", "config0", "config1", "config2", "small_instance",
-    "column_offsets",
+    "unit_columns", "Instance", "config0", "config1", "config2", "config3", "config3_sizes",
+    "batch_instance", "small_instance", "column_offsets",
 ]

@@ -11,6 +11,12 @@ config1: n = 4096, quasi-triangular T with 1024 real eigenvalues U[-n, n] and
          drawn from the prescribed eigenvalues, in a seeded mixed order.
 config2: n = 8192, real eigenvalues U[-n, n] with minimum gap >= 1e-2, 2048
          real shifts.
+config3: 256 independent instances, n = round(exp(U[ln 64, ln 2048])) each,
+         from their own seeds.  A quarter (by a seeded draw) carry complex
+         pairs with the config1 recipe (a quarter of the eigenvalues real);
+         the others follow config0 at size n (n real eigenvalues evenly
+         spaced in [-n, n] with U(-0.1, 0.1) jitter).  Every instance's
+         shifts are all of its real eigenvalues.
 small_instance: the config1 recipe at any size, for parity tests.
 
 Layout conventions (those of the C ABI): H, Q0 and B are column-major; a real
@@ -155,3 +161,35 @@ def small_instance(n, m_real, m_cplx, seed, keep_a=False):
     n_pairs = (n - n_real) // 2
     assert m_cplx <= n_pairs and m_real <= n_real
     return _mixed_instance("small_n%d" % n, n, n_real, m_real, m_cplx, seed, keep_a)
+
+
+S_SIZE, S_KIND = 20, 21
+
+
+def config3_sizes(seed=3, count=256, lo=64, hi=2048):
+    """(n, has_complex) of every instance of the batching workload."""
+    u = uniform(seed, S_SIZE, count)
+    ns = np.rint(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(int)
+    kinds = uniform(seed, S_KIND, count) < 0.25
+    return [(int(n), bool(k)) for n, k in zip(ns, kinds)]
+
+
+def batch_instance(n, has_complex, seed):
+    """One instance of the batching workload (see config3)."""
+    if has_complex:
+        n_real = max(2, n // 4)
+        if (n - n_real) % 2:
+            n_real += 1
+        return _mixed_instance("batch_n%d" % n, n, n_real, n_real, 0, seed, False)
+    eigs = np.linspace(-float(n), float(n), n) + uniform(seed, S_JIT, n, -0.1, 0.1)
+    T, _ = quasi_triangular(n, eigs, [], seed)
+    inst = _build("batch_n%d" % n, n, T, seed, eigs, np.zeros(n), False)
+    inst.eigs = eigs.astype(np.complex128)
+    return inst
+
+
+def config3(seed=3, count=256, lo=64, hi=2048):
+    """The batching workload: a list of instances (seed of instance i is
+    1000 * seed + i + 1)."""
+    return [batch_instance(n, k, 1000 * seed + i + 1)
+            for i, (n, k) in enumerate(config3_sizes(seed, count, lo, hi))]

@@ -222,6 +222,80 @@ hsein_status hsein_plan_destroy(hsein_plan_t plan);
 /* Static, human-readable text for a status code. */
 const char *hsein_status_string(hsein_status status);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent instances (matrices of different n and shift
+ * counts) in one CUDA graph.  The paper solves one matrix at a time; it
+ * groups the shifts of one matrix into blocks that reuse a bounded
+ * workspace (Sec. 4.4, Alg. "hsrq3infinal").  Here every instance, or every
+ * block of its shifts, is a sub-problem with its own plan and slice of one
+ * workspace; the sub-problems are spread over `streams` concurrent chains
+ * (longest first, each to the least loaded chain) and captured once into a
+ * CUDA graph, which every hsein_batch_solve replays.
+ * ------------------------------------------------------------------------ */
+typedef struct hsein_batch_s *hsein_batch_t;
+
+/* one instance: the arguments of hsein_solve (device pointers; dB may be
+ * NULL for rho*e).  The pointers are fixed at hsein_batch_plan; the caller
+ * refreshes the data in place between solves.  Which shifts are complex
+ * (dWi != 0) is read once, at hsein_batch_plan, and must not change. */
+typedef struct {
+    int n, m_real, m_cplx;
+    const double *dH;
+    int ldh;
+    const double *dWr, *dWi;
+    const double *dB;
+    int ldb;
+    double *dX;
+    int ldx;
+    int *dStatus;
+} hsein_instance;
+
+/* tunables of a batch (hsein_batch_autotune searches them) */
+typedef struct {
+    int streams;     /* concurrent chains in the graph, 1..64; 0 = 16               */
+    int br_policy;   /* tile height b_r by n: 0 = 64 for every n; 1 = 32 below       */
+                     /* n = 512, else 64; 2 = 16 below 256, 32 below 1024, else 64    */
+    int shift_block; /* at most this many shifts per sub-problem (a complex shift     */
+                     /* counts once); 0 = all shifts of an instance in one            */
+    int reserved;
+} hsein_batch_config;
+
+/*
+ * Plan a batch of `count` instances (host array inst, copied).  opt applies
+ * to every sub-problem except its tile height, which cfg->br_policy sets (opt
+ * NULL = defaults; cfg NULL = {16, 1, 0}).  Reads every instance's dWi
+ * (synchronously) to lay out the shift blocks.  *workspace_bytes receives the
+ * size of the one device workspace hsein_batch_solve needs for this
+ * configuration and for every configuration hsein_batch_autotune may pick.
+ */
+hsein_status hsein_batch_plan(hsein_batch_t *batch, int count, const hsein_instance *inst,
+                              const hsein_options *opt, const hsein_batch_config *cfg,
+                              size_t *workspace_bytes);
+
+/*
+ * Solve every instance: the results and statuses of each instance are those
+ * hsein_solve gives for it alone with the same options and tile height.  The
+ * first call for a workspace address captures the CUDA graph (on `stream`,
+ * with forks to the batch's own streams); later calls only launch it.
+ * Stream-ordered, asynchronous.
+ */
+hsein_status hsein_batch_solve(hsein_batch_t batch, void *dWork, size_t work_bytes, void *stream);
+
+/*
+ * Autotuner: times the batch (graph replays, CUDA events on `stream`) under
+ * each configuration of a fixed candidate set (tile-height policies x shift
+ * block widths x chain counts), keeps the fastest for later solves and
+ * returns it in *chosen (may be NULL) and its time in *ms (may be NULL).
+ * Synchronizes `stream`; the instances' outputs hold the last trial's results.
+ */
+hsein_status hsein_batch_autotune(hsein_batch_t batch, void *dWork, size_t work_bytes,
+                                  void *stream, hsein_batch_config *chosen, double *ms);
+
+/* the configuration in use and the number of sub-problems / chains */
+hsein_status hsein_batch_info(hsein_batch_t batch, hsein_batch_config *cfg, int *subproblems);
+
+hsein_status hsein_batch_destroy(hsein_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

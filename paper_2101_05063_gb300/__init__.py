@@ -22,7 +22,8 @@ from . import build as _build
 __all__ = [
     "HseinError", "HseinOptions", "load", "hsein_default_options", "hsein_plan", "hsein_solve",
     "hsein_solve_noalloc", "hsein_backtransform", "hsein_plan_sync_status", "hsein_margins",
-    "hsein_restart",
+    "hsein_restart", "hsein_batch_plan", "hsein_batch_solve", "hsein_batch_autotune",
+    "hsein_batch_info", "hsein_batch_destroy", "HseinInstance", "HseinBatchConfig", "Batch",
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
     "STATUS", "PHASES",
@@ -44,6 +45,23 @@ class HseinError(RuntimeError):
 class HseinOptions(ctypes.Structure):
     _fields_ = [("br", ctypes.c_int), ("precision", ctypes.c_int), ("robust", ctypes.c_int),
                 ("omega_log2", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class HseinInstance(ctypes.Structure):
+    """One instance of a batch: the arguments of hsein_solve."""
+    _fields_ = [("n", ctypes.c_int), ("m_real", ctypes.c_int), ("m_cplx", ctypes.c_int),
+                ("dH", ctypes.c_void_p), ("ldh", ctypes.c_int), ("dWr", ctypes.c_void_p),
+                ("dWi", ctypes.c_void_p), ("dB", ctypes.c_void_p), ("ldb", ctypes.c_int),
+                ("dX", ctypes.c_void_p), ("ldx", ctypes.c_int), ("dStatus", ctypes.c_void_p)]
+
+
+class HseinBatchConfig(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int), ("br_policy", ctypes.c_int),
+                ("shift_block", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"streams": self.streams, "br_policy": self.br_policy,
+                "shift_block": self.shift_block}
 
 
 _lib = None
@@ -77,6 +95,18 @@ def load(build_if_missing=True):
     lib.hsein_plan_sync_status.argtypes = [vp, vp, vp]
     lib.hsein_margins.restype = ctypes.c_int
     lib.hsein_margins.argtypes = [vp, vp, dp, vp]
+    bp = ctypes.POINTER(HseinBatchConfig)
+    lib.hsein_batch_plan.restype = ctypes.c_int
+    lib.hsein_batch_plan.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(HseinInstance),
+                                     ctypes.POINTER(HseinOptions), bp, ctypes.POINTER(sz)]
+    lib.hsein_batch_solve.restype = ctypes.c_int
+    lib.hsein_batch_solve.argtypes = [vp, vp, sz, vp]
+    lib.hsein_batch_autotune.restype = ctypes.c_int
+    lib.hsein_batch_autotune.argtypes = [vp, vp, sz, vp, bp, ctypes.POINTER(ctypes.c_double)]
+    lib.hsein_batch_info.restype = ctypes.c_int
+    lib.hsein_batch_info.argtypes = [vp, bp, ctypes.POINTER(ctypes.c_int)]
+    lib.hsein_batch_destroy.restype = ctypes.c_int
+    lib.hsein_batch_destroy.argtypes = [vp]
     lib.hsein_restart.restype = ctypes.c_int
     lib.hsein_restart.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, ip,
                                   ctypes.POINTER(ctypes.c_int), vp, sz, vp]
@@ -148,6 +178,42 @@ def hsein_restart(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, max_tries,
     rc = load().hsein_restart(plan, dH, ldh, dWr, dWi, dB or None, ldb, dX, ldx, dStatus,
                               int(max_tries), ctypes.byref(k), dWork, work_bytes, stream or None)
     return rc, k.value
+
+
+def hsein_batch_plan(instances, opt=None, cfg=None):
+    """instances: a sequence of HseinInstance.  Returns (batch, workspace bytes)."""
+    arr = (HseinInstance * len(instances))(*instances)
+    b = ctypes.c_void_p()
+    w = ctypes.c_size_t()
+    rc = load().hsein_batch_plan(ctypes.byref(b), len(instances), arr,
+                                 ctypes.byref(opt) if opt is not None else None,
+                                 ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(w))
+    _check(rc, "hsein_batch_plan")
+    return b, w.value
+
+
+def hsein_batch_solve(batch, dWork, work_bytes, stream):
+    return load().hsein_batch_solve(batch, dWork, work_bytes, stream or None)
+
+
+def hsein_batch_autotune(batch, dWork, work_bytes, stream):
+    """Returns (status, chosen HseinBatchConfig, ms)."""
+    c = HseinBatchConfig()
+    t = ctypes.c_double()
+    rc = load().hsein_batch_autotune(batch, dWork, work_bytes, stream or None, ctypes.byref(c),
+                                     ctypes.byref(t))
+    return rc, c, t.value
+
+
+def hsein_batch_info(batch):
+    c = HseinBatchConfig()
+    k = ctypes.c_int()
+    _check(load().hsein_batch_info(batch, ctypes.byref(c), ctypes.byref(k)), "hsein_batch_info")
+    return c, k.value
+
+
+def hsein_batch_destroy(batch):
+    return load().hsein_batch_destroy(batch)
 
 
 def hsein_plan_info(plan):
@@ -308,3 +374,70 @@ class Solver:
                                  self._stream())
         _check(rc, "hsein_backtransform")
         return Z
+
+
+class Batch:
+    """Independent instances solved together in one captured CUDA graph
+    (hsein_batch_*).  instances: a list of (H, wr, wi, B or None) CUDA float64
+    tensors; X and status tensors are allocated here (column-major X per
+    instance).  The tensors are referenced, not copied: refresh their
+    contents in place between solves."""
+
+    def __init__(self, instances, streams=16, br_policy=1, shift_block=0, robust=True,
+                 omega_log2=1000, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self._keep = []
+        self.X, self.status = [], []
+        items = []
+        for (H, wr, wi, B) in instances:
+            H = _colmajor(H, torch)
+            wr = wr.to(torch.float64).contiguous()
+            wi = wi.to(torch.float64).contiguous()
+            B = _colmajor(B, torch) if B is not None else None
+            n = H.shape[0]
+            mc = int((wi != 0).sum().item())
+            mr = wr.numel() - mc
+            X = torch.zeros((mr + 2 * mc, n), dtype=torch.float64, device=self.device).t()
+            st = torch.zeros(mr + mc, dtype=torch.int32, device=self.device)
+            self._keep += [H, wr, wi, B]
+            self.X.append(X)
+            self.status.append(st)
+            items.append(HseinInstance(n, mr, mc, H.data_ptr(), _ld(H), wr.data_ptr(),
+                                       wi.data_ptr(), B.data_ptr() if B is not None else None,
+                                       _ld(B) if B is not None else n, X.data_ptr(), _ld(X),
+                                       st.data_ptr()))
+        opt = hsein_default_options()
+        opt.robust = int(bool(robust))
+        opt.omega_log2 = int(omega_log2)
+        cfg = HseinBatchConfig(int(streams), int(br_policy), int(shift_block), 0)
+        with torch.cuda.device(self.device):
+            self.batch, self.work_bytes = hsein_batch_plan(items, opt, cfg)
+        self.work = torch.empty(self.work_bytes, dtype=torch.uint8, device=self.device)
+
+    def __del__(self):
+        b = getattr(self, "batch", None)
+        if b is not None and _lib is not None:
+            _lib.hsein_batch_destroy(b)
+            self.batch = None
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def solve(self):
+        """Solve every instance (one graph launch); returns (X list, status list)."""
+        _check(hsein_batch_solve(self.batch, self.work.data_ptr(), self.work_bytes, self._stream()),
+               "hsein_batch_solve")
+        return self.X, self.status
+
+    def autotune(self):
+        """Search the batch configurations; returns (config dict, ms)."""
+        rc, c, ms = hsein_batch_autotune(self.batch, self.work.data_ptr(), self.work_bytes,
+                                         self._stream())
+        _check(rc, "hsein_batch_autotune")
+        return c.as_dict(), ms
+
+    def info(self):
+        c, k = hsein_batch_info(self.batch)
+        return c.as_dict(), k

@@ -735,15 +735,16 @@ void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, i
     }
 }
 
-// dynamic shared memory above 48 KB needs an opt-in per kernel
+// dynamic shared memory above 48 KB needs an opt-in per kernel; the limit is
+// per kernel instance, not per plan, so each instance is configured for the
+// largest tile height it serves (plans of different heights coexist)
 cudaError_t diag_configure(int br) {
-    const int smem = (int)diag_smem(br);
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     switch (pow2_at_least((br + kLpsR - 1) / kLpsR)) {
-        case 1: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 1>, a, smem);
-        case 2: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 2>, a, smem);
-        case 4: return cudaFuncSetAttribute(k_diag<kLpsC, 2, kLpsR, 4>, a, smem);
-        default: return cudaFuncSetAttribute(k_diag<kLpsC, 4, kLpsR, 8>, a, smem);
+        case 1: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 1>, a, (int)diag_smem(kLpsR));
+        case 2: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 2>, a, (int)diag_smem(2 * kLpsR));
+        case 4: return cudaFuncSetAttribute(k_diag<kLpsC, 2, kLpsR, 4>, a, (int)diag_smem(4 * kLpsR));
+        default: return cudaFuncSetAttribute(k_diag<kLpsC, 4, kLpsR, 8>, a, (int)diag_smem(kMaxBr));
     }
 }
 

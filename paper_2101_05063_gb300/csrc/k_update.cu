@@ -166,8 +166,11 @@ void launch_update(const Layout& L, void* work, const double* H, int ldh, int J,
     k_update<<<grid, 256, smem, s>>>(L, work, H, ldh, J);
 }
 
+// the limit is per kernel, not per plan: configure it for the largest tile
+// height, so that plans of different heights can be used in any order
 cudaError_t update_configure(int br) {
-    size_t smem = 2 * (size_t)br * kTM * sizeof(double);
+    (void)br;
+    size_t smem = 2 * (size_t)kMaxBr * kTM * sizeof(double);
     if (smem < 2 * 16 * 32 * sizeof(double)) smem = 2 * 16 * 32 * sizeof(double);
     return cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
