@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--br", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=256, help="shifts in the oracle sample")
     return ap.parse_args()
 
@@ -249,6 +251,43 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_batch(args, torch, hs, hi):
+    """The batching workload (256 independent instances, n log-uniform in
+    [64, 2048], all real eigenvalues as shifts, FP64 throughout) in one
+    captured CUDA graph per batch, configuration chosen by the autotuner."""
+    import numpy as np
+    t0 = time.perf_counter()
+    insts = hi.config3(workers=min(16, os.cpu_count() or 1))
+    t_gen = time.perf_counter() - t0
+    f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device="cuda")
+    dev = [(f(i.H), f(i.wr), f(i.wi), f(i.B)) for i in insts]
+    b = hs.Batch(dev, streams=16, br_policy=1)
+    cfg, ms_tune = b.autotune()
+    b.solve()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.batch_steps):
+        b.solve()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.batch_steps)]
+    conv = sum(int((st.cpu().numpy() == 0).sum()) for st in b.status)  # real shifts: 1 column each
+    total = sum(i.m for i in insts)
+    ms = float(np.mean(per))
+    return {"workload": "256 independent instances, n = round(exp(U[ln 64, ln 2048])), 25%% with "
+                        "complex pairs, all real eigenvalues as shifts (%d), FP64" % total,
+            "value": conv / (ms * 1e-3), "unit": UNIT, "ms_per_batch": ms,
+            "latency": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                        "unit": "ms", "of": "%d batches" % args.batch_steps},
+            "converged_columns": conv, "columns": total, "autotuned": cfg,
+            "autotune_ms_best": ms_tune, "host_launches_per_batch": 1,
+            "generation_s": t_gen, "sizes": {"min": min(i.n for i in insts),
+                                             "max": max(i.n for i in insts),
+                                             "sum": sum(i.n for i in insts)}}
 
 
 def workload_config(inst, br):
@@ -468,6 +507,8 @@ def main():
         "restart": restart,
         "split_precision": split,
     }
+    if not args.no_batch and world == 1:
+        line["batching"] = measure_batch(args, torch, hs, hi)
     if not args.no_cpu_baseline and world == 1:
         v, cores, desc = cpu_baseline(inst, args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",

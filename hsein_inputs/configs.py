@@ -188,8 +188,36 @@ def batch_instance(n, has_complex, seed):
     return inst
 
 
-def config3(seed=3, count=256, lo=64, hi=2048):
+def _batch_instance_star(args):
+    return batch_instance(*args)
+
+
+def config3(seed=3, count=256, lo=64, hi=2048, workers=0):
     """The batching workload: a list of instances (seed of instance i is
-    1000 * seed + i + 1)."""
-    return [batch_instance(n, k, 1000 * seed + i + 1)
+    1000 * seed + i + 1).  workers > 1 generates them in a pool of spawned
+    processes with single-threaded BLAS; the BLAS thread count changes the
+    summation order, so those instances equal the serial ones only up to
+    rounding (each is still a valid instance of the recipe)."""
+    args = [(n, k, 1000 * seed + i + 1)
             for i, (n, k) in enumerate(config3_sizes(seed, count, lo, hi))]
+    if workers and workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import os
+        keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+                # largest first, so that the pool drains evenly
+                order = sorted(range(len(args)), key=lambda i: -args[i][0])
+                done = dict(zip(order, ex.map(_batch_instance_star, [args[i] for i in order])))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        return [done[i] for i in range(len(args))]
+    return [batch_instance(*a) for a in args]

@@ -8,6 +8,8 @@ Sampled shifts are checked against the oracle.  The full batching workload
 (256 instances, n log-uniform in [64, 2048]) is solved once with the residual
 bound on every converged column.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -100,7 +102,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(small_batch):
 
 
 def test_batching_workload_full_size():
-    insts = hi.config3()
+    insts = hi.config3(workers=min(16, os.cpu_count() or 1))
     assert len(insts) == 256
     dev = _dev(insts)
     b = hs.Batch(dev, streams=16, br_policy=1)
