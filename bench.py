@@ -290,6 +290,42 @@ def measure_batch(args, torch, hs, hi):
                                              "sum": sum(i.n for i in insts)}}
 
 
+def replay_stream(srv, pool_dev, reqs, torch):
+    """Replay a request stream in real time on a hs.Server: each request is
+    submitted at its arrival time (seconds after the start) and progress()
+    is driven in between.  Graded requests run with FP64 products (one digit
+    exponent per row cannot hold their 10^300 range within a row), the
+    others with split-precision products.  Returns per request (arrival,
+    completion) host times in seconds since the start, and the results
+    {request index: (X, status)}."""
+    f = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    shifts = [(f(r["wr"]), f(r["wi"])) for r in reqs]
+    torch.cuda.synchronize()
+    t_done = [None] * len(reqs)
+    of = {}
+    results = {}
+    t0 = time.perf_counter()
+    i = 0
+    while len(results) < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i]["t"] <= now:
+            r = reqs[i]
+            H, Hg = pool_dev[r["n"]][r["index"]]
+            tk = srv.submit(Hg if r["graded"] else H, shifts[i][0], shifts[i][1],
+                            precision=0 if r["graded"] else 1)
+            of[tk] = i
+            i += 1
+        done = srv.progress(wait=(i == len(reqs)))
+        now = time.perf_counter() - t0
+        for tk in done:
+            j = of.pop(tk)
+            t_done[j] = now
+            results[j] = srv.result(tk)
+        if not done and i < len(reqs):
+            time.sleep(max(0.0, min(reqs[i]["t"] - now, 2e-4)))
+    return [(r["t"], t_done[j]) for j, r in enumerate(reqs)], results
+
+
 def workload_config(inst, br):
     return {
         "workload": "mixed real/complex shifts: n=4096, 512 real + 256 complex shifts "

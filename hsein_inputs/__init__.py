@@ -34,6 +34,9 @@ from .configs import (
     config3,
     config3_sizes,
     batch_instance,
+    serving_pool,
+    serving_requests,
+    SERVE_SIZES,
     small_instance,
     column_offsets,
 )
@@ -42,5 +45,6 @@ __all__ = [
     "splitmix64", "uniform", "normal", "haar_orthogonal", "quasi_triangular",
     "hessenberg_reduce", "paper_h2", "paper_h3", "paper_r2_q2", "companion", "graded",
     "unit_columns", "Instance", "config0", "config1", "config2", "config3", "config3_sizes",
-    "batch_instance", "small_instance", "column_offsets",
+    "batch_instance", "serving_pool", "serving_requests", "SERVE_SIZES", "small_instance",
+    "column_offsets",
 ]

@@ -221,3 +221,67 @@ def config3(seed=3, count=256, lo=64, hi=2048, workers=0):
                     os.environ[k] = v
         return [done[i] for i in range(len(args))]
     return [batch_instance(*a) for a in args]
+
+
+# --------------------------------------------------------------- serving
+S_ARRIVE, S_CLASS, S_PICK, S_K, S_KIND4, S_GRADE4, S_SHIFTS4 = 30, 31, 32, 33, 34, 35, 36
+SERVE_SIZES = (256, 512, 1024, 2048, 4096, 8192)
+
+
+def serving_pool(sizes=SERVE_SIZES, per_size=None, seed=4):
+    """{n: [instances]}: the matrix pool of the serving workload.  Each is the
+    config1 recipe at size n (a quarter of the eigenvalues real, the rest in
+    complex pairs); per_size[n] instances per class (default 8 up to n = 2048,
+    2 at 4096, 1 at 8192).  Each instance also carries its graded form
+    D H D^-1, D = diag(10^u), u ~ U[-150, 150] per index (attribute Hg)."""
+    from .matrices import S_GRADE
+    pool = {}
+    for n in sizes:
+        k = (per_size or {}).get(n, 8 if n <= 2048 else (2 if n <= 4096 else 1))
+        lst = []
+        for j in range(k):
+            s = 100000 * seed + 100 * n + j
+            n_real = n // 4 + ((n - n // 4) % 2)
+            inst = _mixed_instance("serve_n%d_%d" % (n, j), n, n_real, 0, 0, s, False)
+            u = uniform(s, S_GRADE, n, -150.0, 150.0)
+            d = 10.0 ** u
+            inst.Hg = np.asfortranarray(inst.H * d[:, None] / d[None, :])
+            inst.n_real = n_real
+            lst.append(inst)
+        pool[n] = lst
+    return pool
+
+
+def serving_requests(pool, count, seed=4, rate=200.0):
+    """The request stream: Poisson arrivals (rate per second), n uniform over
+    the pool's size classes, a pool instance uniform in its class, k shifts
+    uniform in [1, n/4]; 30% graded (the instance's D H D^-1), 30% with
+    complex pairs (ceil(k/2) complex shifts, one member per pair, and
+    floor(k/2) real ones), the rest k real shifts; shifts drawn without
+    replacement from the instance's eigenvalues.  Starting vectors: rho e.
+    Returns a list of dicts (t, n, index, graded, wr, wi)."""
+    sizes = sorted(pool)
+    ua = uniform(seed, S_ARRIVE, count)
+    t = np.cumsum(-np.log(1.0 - ua) / rate)
+    cls = (uniform(seed, S_CLASS, count) * len(sizes)).astype(int)
+    pick = uniform(seed, S_PICK, count)
+    uk = uniform(seed, S_K, count)
+    kind = uniform(seed, S_KIND4, count)
+    grade = uniform(seed, S_GRADE4, count)
+    reqs = []
+    for i in range(count):
+        n = sizes[cls[i]]
+        idx = int(pick[i] * len(pool[n]))
+        inst = pool[n][idx]
+        k = 1 + int(uk[i] * (n // 4))
+        cplx = kind[i] < 0.3
+        kc, kr = ((k + 1) // 2, k // 2) if cplx else (0, k)
+        reals = inst.eigs[:inst.n_real].real
+        pairs = inst.eigs[inst.n_real:inst.n_real + (n - inst.n_real) // 2]
+        pr = np.argsort(uniform(seed * 7919 + i, S_SHIFTS4, len(reals)), kind="stable")[:kr]
+        pc = np.argsort(uniform(seed * 7919 + i, S_SHIFTS4, len(pairs), start=n), kind="stable")[:kc]
+        wr = np.concatenate([reals[pr], pairs[pc].real])
+        wi = np.concatenate([np.zeros(kr), pairs[pc].imag])
+        reqs.append({"t": float(t[i]), "n": n, "index": idx, "graded": bool(grade[i] < 0.3),
+                     "wr": wr, "wi": wi})
+    return reqs

@@ -296,6 +296,61 @@ hsein_status hsein_batch_info(hsein_batch_t batch, hsein_batch_config *cfg, int 
 
 hsein_status hsein_batch_destroy(hsein_batch_t batch);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  The paper has no
+ * counterpart; it is the deployment of the solver for a stream of requests.
+ * The server owns one device arena (hbm_bytes) for solve workspaces and a
+ * pool of streams.  hsein_server_progress retires finished solves, then
+ * admits pending requests in arrival order while a stream is free and the
+ * arena can hold their workspace: requests on the same matrix (same dH, n,
+ * precision, and all with or all without starting vectors) that are pending
+ * together are fused into one solve of their shift sets (the shared-H
+ * updates then serve all of them), up to max_merge_shifts shifts.  Work of
+ * admitted solves overlaps on the device; results are scattered back to each
+ * request's own dX / dStatus and equal those of hsein_solve on the request
+ * alone (columns never mix).  Single-threaded: the caller drives it.
+ * ------------------------------------------------------------------------ */
+typedef struct hsein_server_s *hsein_server_t;
+
+typedef struct {
+    hsein_instance inst; /* the solve; its buffers stay valid until the ticket completes */
+    int precision;       /* 0 FP64 products, 1 split-precision products (b_r 64)          */
+    int br;              /* tile height for precision 0 (0 = 64)                          */
+} hsein_request;
+
+/*
+ * hbm_bytes: device memory the server allocates once for workspaces and the
+ * fused requests' gathered shifts, starting vectors and results; max_jobs:
+ * solves in flight at once (1..64); max_merge_shifts: the most shifts fused
+ * into one solve (>= 1).  opt: robust / omega_log2 for every solve (NULL:
+ * defaults).
+ */
+hsein_status hsein_server_create(hsein_server_t *server, size_t hbm_bytes, int max_jobs,
+                                 int max_merge_shifts, const hsein_options *opt);
+
+/* queue a request (copied); *ticket identifies it in hsein_server_progress.
+ * HSEIN_ENOMEM if its footprint alone exceeds the arena. */
+hsein_status hsein_server_submit(hsein_server_t server, const hsein_request *req,
+                                 long long *ticket);
+
+/*
+ * Retire finished solves and admit pending requests.  The tickets completed
+ * since the last call are written to done[0 .. *n_done) (at most max_done;
+ * the rest are reported by later calls).  wait != 0 blocks until at least
+ * one solve finishes when solves are in flight and none has finished yet.
+ */
+hsein_status hsein_server_progress(hsein_server_t server, long long *done, int max_done,
+                                   int *n_done, int wait);
+
+/* requests pending admission, solves in flight, arena bytes in use,
+ * requests fused into the solves admitted so far and those solves' count */
+hsein_status hsein_server_stats(hsein_server_t server, int *pending, int *running,
+                                size_t *bytes_in_use, long long *requests_admitted,
+                                long long *solves_admitted);
+
+/* waits for the solves in flight, then frees everything */
+hsein_status hsein_server_destroy(hsein_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

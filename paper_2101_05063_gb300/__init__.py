@@ -24,6 +24,8 @@ __all__ = [
     "hsein_solve_noalloc", "hsein_backtransform", "hsein_plan_sync_status", "hsein_margins",
     "hsein_restart", "hsein_batch_plan", "hsein_batch_solve", "hsein_batch_autotune",
     "hsein_batch_info", "hsein_batch_destroy", "HseinInstance", "HseinBatchConfig", "Batch",
+    "HseinRequest", "hsein_server_create", "hsein_server_submit", "hsein_server_progress",
+    "hsein_server_stats", "hsein_server_destroy", "Server",
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
     "STATUS", "PHASES",
@@ -53,6 +55,10 @@ class HseinInstance(ctypes.Structure):
                 ("dH", ctypes.c_void_p), ("ldh", ctypes.c_int), ("dWr", ctypes.c_void_p),
                 ("dWi", ctypes.c_void_p), ("dB", ctypes.c_void_p), ("ldb", ctypes.c_int),
                 ("dX", ctypes.c_void_p), ("ldx", ctypes.c_int), ("dStatus", ctypes.c_void_p)]
+
+
+class HseinRequest(ctypes.Structure):
+    _fields_ = [("inst", HseinInstance), ("precision", ctypes.c_int), ("br", ctypes.c_int)]
 
 
 class HseinBatchConfig(ctypes.Structure):
@@ -107,6 +113,18 @@ def load(build_if_missing=True):
     lib.hsein_batch_info.argtypes = [vp, bp, ctypes.POINTER(ctypes.c_int)]
     lib.hsein_batch_destroy.restype = ctypes.c_int
     lib.hsein_batch_destroy.argtypes = [vp]
+    ll = ctypes.c_longlong
+    lib.hsein_server_create.restype = ctypes.c_int
+    lib.hsein_server_create.argtypes = [ctypes.POINTER(vp), sz, ip, ip, ctypes.POINTER(HseinOptions)]
+    lib.hsein_server_submit.restype = ctypes.c_int
+    lib.hsein_server_submit.argtypes = [vp, ctypes.POINTER(HseinRequest), ctypes.POINTER(ll)]
+    lib.hsein_server_progress.restype = ctypes.c_int
+    lib.hsein_server_progress.argtypes = [vp, ctypes.POINTER(ll), ip, ctypes.POINTER(ip), ip]
+    lib.hsein_server_stats.restype = ctypes.c_int
+    lib.hsein_server_stats.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                       ctypes.POINTER(sz), ctypes.POINTER(ll), ctypes.POINTER(ll)]
+    lib.hsein_server_destroy.restype = ctypes.c_int
+    lib.hsein_server_destroy.argtypes = [vp]
     lib.hsein_restart.restype = ctypes.c_int
     lib.hsein_restart.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, ip,
                                   ctypes.POINTER(ctypes.c_int), vp, sz, vp]
@@ -214,6 +232,44 @@ def hsein_batch_info(batch):
 
 def hsein_batch_destroy(batch):
     return load().hsein_batch_destroy(batch)
+
+
+def hsein_server_create(hbm_bytes, max_jobs, max_merge_shifts, opt=None):
+    srv = ctypes.c_void_p()
+    rc = load().hsein_server_create(ctypes.byref(srv), int(hbm_bytes), int(max_jobs),
+                                    int(max_merge_shifts),
+                                    ctypes.byref(opt) if opt is not None else None)
+    _check(rc, "hsein_server_create")
+    return srv
+
+
+def hsein_server_submit(server, req):
+    """Returns (status, ticket)."""
+    t = ctypes.c_longlong()
+    rc = load().hsein_server_submit(server, ctypes.byref(req), ctypes.byref(t))
+    return rc, t.value
+
+
+def hsein_server_progress(server, max_done=256, wait=False):
+    """Returns (status, list of completed tickets)."""
+    buf = (ctypes.c_longlong * max_done)()
+    k = ctypes.c_int()
+    rc = load().hsein_server_progress(server, buf, max_done, ctypes.byref(k), int(bool(wait)))
+    return rc, list(buf[:k.value])
+
+
+def hsein_server_stats(server):
+    p, r = ctypes.c_int(), ctypes.c_int()
+    b = ctypes.c_size_t()
+    ra, sa = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().hsein_server_stats(server, ctypes.byref(p), ctypes.byref(r), ctypes.byref(b),
+                                     ctypes.byref(ra), ctypes.byref(sa)), "hsein_server_stats")
+    return {"pending": p.value, "running": r.value, "bytes_in_use": b.value,
+            "requests_admitted": ra.value, "solves_admitted": sa.value}
+
+
+def hsein_server_destroy(server):
+    return load().hsein_server_destroy(server)
 
 
 def hsein_plan_info(plan):
@@ -441,3 +497,65 @@ class Batch:
     def info(self):
         c, k = hsein_batch_info(self.batch)
         return c.as_dict(), k
+
+
+class Server:
+    """The serving loop (hsein_server_*): submit requests, drive progress().
+
+    submit(H, wr, wi, B=None, precision=0, br=64) takes CUDA float64 tensors
+    (kept alive until the request completes), allocates its X and status and
+    returns a ticket; progress() returns the tickets completed since the last
+    call; result(ticket) gives (X, status) of a completed request."""
+
+    def __init__(self, hbm_bytes, max_jobs=8, max_merge_shifts=4096, robust=True,
+                 omega_log2=1000, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        opt = hsein_default_options()
+        opt.robust = int(bool(robust))
+        opt.omega_log2 = int(omega_log2)
+        with torch.cuda.device(self.device):
+            self.server = hsein_server_create(hbm_bytes, max_jobs, max_merge_shifts, opt)
+        self._live = {}
+
+    def __del__(self):
+        srv = getattr(self, "server", None)
+        if srv is not None and _lib is not None:
+            _lib.hsein_server_destroy(srv)
+            self.server = None
+
+    def submit(self, H, wr, wi, B=None, precision=0, br=64):
+        torch = self.torch
+        H = _colmajor(H, torch)
+        wr = wr.to(torch.float64).contiguous()
+        wi = wi.to(torch.float64).contiguous()
+        B = _colmajor(B, torch) if B is not None else None
+        n = H.shape[0]
+        mc = int((wi != 0).sum().item())
+        mr = wr.numel() - mc
+        X = torch.empty((mr + 2 * mc, n), dtype=torch.float64, device=self.device).t()
+        st = torch.empty(mr + mc, dtype=torch.int32, device=self.device)
+        inst = HseinInstance(n, mr, mc, H.data_ptr(), _ld(H), wr.data_ptr(), wi.data_ptr(),
+                             B.data_ptr() if B is not None else None,
+                             _ld(B) if B is not None else n, X.data_ptr(), _ld(X), st.data_ptr())
+        # the library's streams wait for nothing of torch's: make the inputs ready
+        torch.cuda.current_stream(self.device).synchronize()
+        rc, t = hsein_server_submit(self.server, HseinRequest(inst, int(precision), int(br)))
+        _check(rc, "hsein_server_submit")
+        self._live[t] = (H, wr, wi, B, X, st)
+        return t
+
+    def progress(self, wait=False):
+        rc, done = hsein_server_progress(self.server, 4096, wait)
+        _check(rc, "hsein_server_progress")
+        return done
+
+    def result(self, ticket):
+        """(X, status) of a completed request (released from the server's
+        bookkeeping)."""
+        H, wr, wi, B, X, st = self._live.pop(ticket)
+        return X, st
+
+    def stats(self):
+        return hsein_server_stats(self.server)
