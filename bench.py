@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-requests", type=int, default=4000,
+                    help="requests in the serving stream (the full workload is 20000)")
     ap.add_argument("--cpu-sample", type=int, default=256, help="shifts in the oracle sample")
     return ap.parse_args()
 
@@ -290,14 +293,14 @@ def measure_batch(args, torch, hs, hi):
                                              "sum": sum(i.n for i in insts)}}
 
 
-def replay_stream(srv, pool_dev, reqs, torch):
+def replay_stream(srv, pool_dev, reqs, torch, keep=True):
     """Replay a request stream in real time on a hs.Server: each request is
     submitted at its arrival time (seconds after the start) and progress()
     is driven in between.  Graded requests run with FP64 products (one digit
     exponent per row cannot hold their 10^300 range within a row), the
     others with split-precision products.  Returns per request (arrival,
     completion) host times in seconds since the start, and the results
-    {request index: (X, status)}."""
+    {request index: (X, status)} (keep=False: only the status, on the host)."""
     f = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
     shifts = [(f(r["wr"]), f(r["wi"])) for r in reqs]
     torch.cuda.synchronize()
@@ -320,10 +323,52 @@ def replay_stream(srv, pool_dev, reqs, torch):
         for tk in done:
             j = of.pop(tk)
             t_done[j] = now
-            results[j] = srv.result(tk)
+            X, st = srv.result(tk)
+            results[j] = (X, st) if keep else st.cpu().numpy()
         if not done and i < len(reqs):
             time.sleep(max(0.0, min(reqs[i]["t"] - now, 2e-4)))
     return [(r["t"], t_done[j]) for j, r in enumerate(reqs)], results
+
+
+def measure_serving(args, torch, hs, hi):
+    """The serving workload: a Poisson stream (200 requests/s) of solves on a
+    pre-generated pool, replayed in real time through hs.Server."""
+    import numpy as np
+    t0 = time.perf_counter()
+    pool = hi.serving_pool()
+    t_gen = time.perf_counter() - t0
+    f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device="cuda")
+    pool_dev = {n: [(f(i.H), f(i.Hg)) for i in lst] for n, lst in pool.items()}
+    reqs = hi.serving_requests(pool, args.serve_requests)
+    srv = hs.Server(64 << 30, max_jobs=8, max_merge_shifts=4096)
+    # warm-up: one request per size class, outside the stream
+    warm = [dict(r, t=0.0) for r in hi.serving_requests(pool, 64, seed=41)]
+    seen, wl = set(), []
+    for r in warm:
+        if (r["n"], r["graded"]) not in seen:
+            seen.add((r["n"], r["graded"]))
+            wl.append(r)
+    replay_stream(srv, pool_dev, wl, torch, keep=False)
+    s0 = srv.stats()
+    times, status = replay_stream(srv, pool_dev, reqs, torch, keep=False)
+    s1 = srv.stats()
+    lat = np.array([c - a for a, c in times]) * 1e3
+    conv = sum(int(sum(2 if w != 0 else 1 for w, st in zip(r["wi"], status[j]) if st == 0))
+               for j, r in enumerate(reqs))
+    cols = sum(len(r["wr"]) + int((r["wi"] != 0).sum()) for r in reqs)
+    span = max(c for a, c in times)
+    return {"workload": "Poisson stream, 200 requests/s, %d requests; n uniform over %s, k "
+                        "uniform in [1, n/4]; 30%% graded D H D^-1 (u ~ U[-150, 150], FP64 "
+                        "products), 30%% with complex pairs; split-precision products otherwise; "
+                        "rho e starting vectors" % (len(reqs), list(hi.SERVE_SIZES)),
+            "value": conv / span, "unit": UNIT, "span_s": span,
+            "latency": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                        "unit": "ms", "of": "%d requests, arrival to completion" % len(reqs)},
+            "converged_columns": conv, "columns": cols,
+            "requests_admitted": s1["requests_admitted"] - s0["requests_admitted"],
+            "solves_admitted": s1["solves_admitted"] - s0["solves_admitted"],
+            "server": {"arena_gb": 64, "max_jobs": 8, "max_merge_shifts": 4096},
+            "pool": {str(n): len(v) for n, v in pool.items()}, "generation_s": t_gen}
 
 
 def workload_config(inst, br):
@@ -545,6 +590,8 @@ def main():
     }
     if not args.no_batch and world == 1:
         line["batching"] = measure_batch(args, torch, hs, hi)
+    if not args.no_serve and world == 1:
+        line["serving"] = measure_serving(args, torch, hs, hi)
     if not args.no_cpu_baseline and world == 1:
         v, cores, desc = cpu_baseline(inst, args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
