@@ -222,6 +222,35 @@ hsein_status hsein_plan_destroy(hsein_plan_t plan);
 /* Static, human-readable text for a status code. */
 const char *hsein_status_string(hsein_status status);
 
+/*
+ * Power-of-two balancing of an upper Hessenberg matrix, so that graded inputs
+ * (rows and columns of very different scale) can use the split-precision
+ * products: integer exponents e with Hb = D^-1 H D, D = diag(2^e) (exact:
+ * every entry is scaled by a power of two; Hb is Hessenberg with the
+ * eigenvalues of H, and x eigenvector of Hb <=> D x eigenvector of H).  The
+ * exponents come from sweeps over i = 1..n that scale row i and column i
+ * by 2^k, k the integer nearest to log2(sqrt(r_i / c_i)) for the
+ * off-diagonal 1-norms r_i (row) and c_i (column), accepted when it lowers
+ * r_i + c_i by at least 5%; the sweeps stop when one changes nothing or after
+ * max_sweeps (the scaling step of Parlett and Reinsch's balancing, radix 2).
+ * dH n x n (ldh >= n); dHb n x n output (ldhb >= n, not aliasing dH; entries
+ * below the subdiagonal are written as 0); dExp n ints.  Stream-ordered.
+ */
+hsein_status hsein_balance(int n, const double *dH, int ldh, double *dHb, int ldhb, int *dExp,
+                           int max_sweeps, void *stream);
+
+/*
+ * Eigenvectors of the balanced matrix back to the original one: every
+ * column (a complex shift's [re, im] pair jointly) becomes D x / ||D x||_2,
+ * computed with exponent arithmetic so that nothing overflows (components
+ * more than 2^1074 below the column's largest flush to 0); zero columns (not
+ * converged) stay zero.  m shifts, dWi their imaginary parts (device; a
+ * nonzero marks a two-column complex shift), dX n x (m_real + 2 m_cplx) in
+ * place.  Stream-ordered.
+ */
+hsein_status hsein_unbalance(int n, int m, const double *dWi, const int *dExp, double *dX,
+                             int ldx, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batches of independent instances (matrices of different n and shift
  * counts) in one CUDA graph.  The paper solves one matrix at a time; it
@@ -316,6 +345,9 @@ typedef struct {
     hsein_instance inst; /* the solve; its buffers stay valid until the ticket completes */
     int precision;       /* 0 FP64 products, 1 split-precision products (b_r 64)          */
     int br;              /* tile height for precision 0 (0 = 64)                          */
+    const int *dExp;     /* NULL, or the exponents of hsein_balance when inst.dH is a      */
+                         /* balanced matrix: the results are then mapped back with        */
+                         /* hsein_unbalance before the ticket completes                    */
 } hsein_request;
 
 /*

@@ -25,7 +25,8 @@ __all__ = [
     "hsein_restart", "hsein_batch_plan", "hsein_batch_solve", "hsein_batch_autotune",
     "hsein_batch_info", "hsein_batch_destroy", "HseinInstance", "HseinBatchConfig", "Batch",
     "HseinRequest", "hsein_server_create", "hsein_server_submit", "hsein_server_progress",
-    "hsein_server_stats", "hsein_server_destroy", "Server",
+    "hsein_server_stats", "hsein_server_destroy", "Server", "hsein_balance", "hsein_unbalance",
+    "balance", "unbalance",
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
     "STATUS", "PHASES",
@@ -58,7 +59,8 @@ class HseinInstance(ctypes.Structure):
 
 
 class HseinRequest(ctypes.Structure):
-    _fields_ = [("inst", HseinInstance), ("precision", ctypes.c_int), ("br", ctypes.c_int)]
+    _fields_ = [("inst", HseinInstance), ("precision", ctypes.c_int), ("br", ctypes.c_int),
+                ("dExp", ctypes.c_void_p)]
 
 
 class HseinBatchConfig(ctypes.Structure):
@@ -114,6 +116,10 @@ def load(build_if_missing=True):
     lib.hsein_batch_destroy.restype = ctypes.c_int
     lib.hsein_batch_destroy.argtypes = [vp]
     ll = ctypes.c_longlong
+    lib.hsein_balance.restype = ctypes.c_int
+    lib.hsein_balance.argtypes = [ip, dp, ip, dp, ip, dp, ip, vp]
+    lib.hsein_unbalance.restype = ctypes.c_int
+    lib.hsein_unbalance.argtypes = [ip, ip, dp, dp, dp, ip, vp]
     lib.hsein_server_create.restype = ctypes.c_int
     lib.hsein_server_create.argtypes = [ctypes.POINTER(vp), sz, ip, ip, ctypes.POINTER(HseinOptions)]
     lib.hsein_server_submit.restype = ctypes.c_int
@@ -232,6 +238,39 @@ def hsein_batch_info(batch):
 
 def hsein_batch_destroy(batch):
     return load().hsein_batch_destroy(batch)
+
+
+def hsein_balance(n, dH, ldh, dHb, ldhb, dExp, max_sweeps, stream):
+    return load().hsein_balance(n, dH, ldh, dHb, ldhb, dExp, max_sweeps, stream or None)
+
+
+def hsein_unbalance(n, m, dWi, dExp, dX, ldx, stream):
+    return load().hsein_unbalance(n, m, dWi, dExp, dX, ldx, stream or None)
+
+
+def balance(H, max_sweeps=30):
+    """Power-of-two balancing of a CUDA float64 Hessenberg matrix: returns
+    (Hb, exps) with Hb = D^-1 H D, D = diag(2^exps), column-major."""
+    import torch
+    H = _colmajor(H, torch)
+    n = H.shape[0]
+    Hb = torch.empty((n, n), dtype=torch.float64, device=H.device).t()
+    e = torch.empty(n, dtype=torch.int32, device=H.device)
+    _check(hsein_balance(n, H.data_ptr(), _ld(H), Hb.data_ptr(), _ld(Hb), e.data_ptr(),
+                         int(max_sweeps), torch.cuda.current_stream(H.device).cuda_stream),
+           "hsein_balance")
+    return Hb, e
+
+
+def unbalance(X, wi, exps):
+    """Eigenvectors of the balanced matrix (in place in X, column-major) back
+    to the original matrix, unit 2-norm per shift."""
+    import torch
+    wi = wi.to(torch.float64).contiguous()
+    _check(hsein_unbalance(X.shape[0], wi.numel(), wi.data_ptr(), exps.data_ptr(), X.data_ptr(),
+                           _ld(X), torch.cuda.current_stream(X.device).cuda_stream),
+           "hsein_unbalance")
+    return X
 
 
 def hsein_server_create(hbm_bytes, max_jobs, max_merge_shifts, opt=None):
@@ -525,7 +564,7 @@ class Server:
             _lib.hsein_server_destroy(srv)
             self.server = None
 
-    def submit(self, H, wr, wi, B=None, precision=0, br=64):
+    def submit(self, H, wr, wi, B=None, precision=0, br=64, exps=None):
         torch = self.torch
         H = _colmajor(H, torch)
         wr = wr.to(torch.float64).contiguous()
@@ -541,9 +580,10 @@ class Server:
                              _ld(B) if B is not None else n, X.data_ptr(), _ld(X), st.data_ptr())
         # the library's streams wait for nothing of torch's: make the inputs ready
         torch.cuda.current_stream(self.device).synchronize()
-        rc, t = hsein_server_submit(self.server, HseinRequest(inst, int(precision), int(br)))
+        rc, t = hsein_server_submit(self.server, HseinRequest(
+            inst, int(precision), int(br), exps.data_ptr() if exps is not None else None))
         _check(rc, "hsein_server_submit")
-        self._live[t] = (H, wr, wi, B, X, st)
+        self._live[t] = (H, wr, wi, B, X, st, exps)
         return t
 
     def progress(self, wait=False):
@@ -554,7 +594,7 @@ class Server:
     def result(self, ticket):
         """(X, status) of a completed request (released from the server's
         bookkeeping)."""
-        H, wr, wi, B, X, st = self._live.pop(ticket)
+        H, wr, wi, B, X, st, exps = self._live.pop(ticket)
         return X, st
 
     def stats(self):

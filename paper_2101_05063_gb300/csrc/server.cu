@@ -106,6 +106,7 @@ int columns(const hsein_request& r) { return r.inst.m_real + 2 * r.inst.m_cplx; 
 // requests that can share one solve
 bool same_solve(const hsein_request& a, const hsein_request& b) {
     return a.inst.dH == b.inst.dH && a.inst.n == b.inst.n && a.inst.ldh == b.inst.ldh &&
+           a.dExp == b.dExp &&
            a.precision == b.precision && a.br == b.br && (a.inst.dB == nullptr) == (b.inst.dB == nullptr);
 }
 
@@ -216,6 +217,13 @@ hsein_status launch(hsein_server_s* S, const std::vector<size_t>& group, hsein_p
             c0 += nc;
         }
         if (rc == HSEIN_OK && !ok) rc = HSEIN_ECUDA;
+    }
+    // eigenvectors of a balanced matrix back to the caller's matrix
+    for (size_t i : group) {
+        if (rc != HSEIN_OK) break;
+        const hsein_request& r = S->pending[i].req;
+        if (r.dExp)
+            rc = hsein_unbalance(n, shifts(r), r.inst.dWi, r.dExp, r.inst.dX, r.inst.ldx, s);
     }
     if (rc == HSEIN_OK && cudaEventRecord(S->events[slot], s) != cudaSuccess) rc = HSEIN_ECUDA;
     return rc;
