@@ -296,9 +296,12 @@ def measure_batch(args, torch, hs, hi):
 def replay_stream(srv, pool_dev, reqs, torch, keep=True):
     """Replay a request stream in real time on a hs.Server: each request is
     submitted at its arrival time (seconds after the start) and progress()
-    is driven in between.  Graded requests run with FP64 products (one digit
-    exponent per row cannot hold their 10^300 range within a row), the
-    others with split-precision products.  Returns per request (arrival,
+    is driven in between.  pool_dev[n][i] = (H, Hb, e): the matrix, the
+    power-of-two balanced form of its graded variant and the balancing
+    exponents.  Every request runs with split-precision products; a graded
+    one on the balanced matrix (one digit exponent per row could not hold
+    the 10^300 range of a graded row), mapped back by the server.  Returns
+    per request (arrival,
     completion) host times in seconds since the start, and the results
     {request index: (X, status)} (keep=False: only the status, on the host)."""
     f = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
@@ -313,9 +316,10 @@ def replay_stream(srv, pool_dev, reqs, torch, keep=True):
         now = time.perf_counter() - t0
         while i < len(reqs) and reqs[i]["t"] <= now:
             r = reqs[i]
-            H, Hg = pool_dev[r["n"]][r["index"]]
-            tk = srv.submit(Hg if r["graded"] else H, shifts[i][0], shifts[i][1],
-                            precision=0 if r["graded"] else 1)
+            H, Hb, e = pool_dev[r["n"]][r["index"]]
+            # graded requests run on the balanced form of their matrix
+            tk = srv.submit(Hb if r["graded"] else H, shifts[i][0], shifts[i][1], precision=1,
+                            exps=e if r["graded"] else None)
             of[tk] = i
             i += 1
         done = srv.progress(wait=(i == len(reqs)))
@@ -338,7 +342,9 @@ def measure_serving(args, torch, hs, hi):
     pool = hi.serving_pool()
     t_gen = time.perf_counter() - t0
     f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device="cuda")
-    pool_dev = {n: [(f(i.H), f(i.Hg)) for i in lst] for n, lst in pool.items()}
+    pool_dev = {n: [(f(i.H),) + tuple(hs.balance(f(i.Hg))) for i in lst]
+                for n, lst in pool.items()}
+    torch.cuda.synchronize()
     reqs = hi.serving_requests(pool, args.serve_requests)
     srv = hs.Server(64 << 30, max_jobs=8, max_merge_shifts=4096)
     # warm-up: one request per size class, outside the stream
@@ -358,9 +364,10 @@ def measure_serving(args, torch, hs, hi):
     cols = sum(len(r["wr"]) + int((r["wi"] != 0).sum()) for r in reqs)
     span = max(c for a, c in times)
     return {"workload": "Poisson stream, 200 requests/s, %d requests; n uniform over %s, k "
-                        "uniform in [1, n/4]; 30%% graded D H D^-1 (u ~ U[-150, 150], FP64 "
-                        "products), 30%% with complex pairs; split-precision products otherwise; "
-                        "rho e starting vectors" % (len(reqs), list(hi.SERVE_SIZES)),
+                        "uniform in [1, n/4]; 30%% graded D H D^-1 (u ~ U[-150, 150]) solved "
+                        "on their power-of-two balanced form; 30%% with complex pairs; "
+                        "split-precision products; rho e starting vectors"
+                        % (len(reqs), list(hi.SERVE_SIZES)),
             "value": conv / span, "unit": UNIT, "span_s": span,
             "latency": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                         "unit": "ms", "of": "%d requests, arrival to completion" % len(reqs)},

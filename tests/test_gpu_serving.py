@@ -29,6 +29,9 @@ GB = 1 << 30
 def pool():
     p = hi.serving_pool(sizes=(256, 512, 1024), per_size={256: 2, 512: 2, 1024: 2}, seed=9)
     dev = {n: [(to_dev(i.H), to_dev(i.Hg)) for i in lst] for n, lst in p.items()}
+    bal = {n: [(to_dev(i.H),) + tuple(hs.balance(to_dev(i.Hg))) for i in lst] for n, lst in p.items()}
+    torch.cuda.synchronize()
+    dev["balanced"] = bal
     return p, dev
 
 
@@ -112,7 +115,7 @@ def test_short_poisson_stream(pool):
     p, dev = pool
     reqs = _requests(p, 120, 14)
     srv = hs.Server(8 * GB, max_jobs=8, max_merge_shifts=4096)
-    times, results = bench.replay_stream(srv, dev, reqs, torch)
+    times, results = bench.replay_stream(srv, dev["balanced"], reqs, torch)
     lat = np.array([c - a for a, c in times])
     assert np.all(lat > 0)
     conv = 0
@@ -122,11 +125,20 @@ def test_short_poisson_stream(pool):
         conv += int(sum(2 if w != 0 else 1 for w, st in zip(r["wi"], sh) if st == 0))
         if j % 10:
             continue
-        # residual of the converged columns (FP64 on the device) and the
-        # result alone, for every tenth request
-        H = dev[r["n"]][r["index"]][1 if r["graded"] else 0]
-        Xa, sa = _alone(H, to_dev(r["wr"]), to_dev(r["wi"]), 0 if r["graded"] else 1)
-        assert np.array_equal(sh, sa) and np.array_equal(X.cpu().numpy(), Xa)
+        # the result alone, for every tenth request; the residual of the
+        # converged columns (FP64 on the device; graded requests in the
+        # balanced basis, where the solve ran)
+        Hp, Hb, e = dev["balanced"][r["n"]][r["index"]]
+        H = Hb if r["graded"] else Hp
+        Xa, sa = _alone(H, to_dev(r["wr"]), to_dev(r["wi"]), 1)
+        if r["graded"]:
+            Xb = to_dev(Xa)
+            hs.unbalance(Xb, to_dev(r["wi"]), e)
+            Xua = Xb.cpu().numpy()
+        else:
+            Xua = Xa
+        assert np.array_equal(sh, sa) and np.array_equal(X.cpu().numpy(), Xua)
+        X = to_dev(Xa)
         offs = hi.column_offsets(r["wi"])
         HX = (H @ X).cpu().numpy()
         Xh = X.cpu().numpy()
