@@ -429,10 +429,12 @@ def main():
             worst = max(worst, np.abs(hx - lam * x).sum() / (hn1 * np.abs(x).sum()))
         return worst / (n * EPS)
 
-    def measure(precision, sample_clocks):
-        """Warm up, check, then time args.steps steps of one precision mode."""
+    def measure(precision, sample_clocks, method=0, steps=None):
+        """Warm up, check, then time `steps` (default args.steps) steps of one
+        precision mode / method."""
+        nsteps = steps or args.steps
         solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=args.br, precision=precision,
-                           device=dev)
+                           device=dev, method=method)
 
         def step():
             solver.solve(dH, dwr, dwi, dB, X=X, status=status, check=False)
@@ -454,17 +456,17 @@ def main():
         barrier(world)
         torch.cuda.synchronize()
         # one event between consecutive steps: per-step latency and the total
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
         evs[0].record(stream)
-        for i in range(args.steps):
+        for i in range(nsteps):
             step()
             evs[i + 1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
         ms = evs[0].elapsed_time(evs[-1])
-        per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(nsteps)]
         lat = {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
-               "unit": "ms", "of": "%d steps" % args.steps}
+               "unit": "ms", "of": "%d steps" % nsteps}
         prof = hs.hsein_plan_profile(solver.plan, reset=True)
         hs.hsein_plan_set_profiling(solver.plan, False)
         clocks = sampler.stop() if sampler else None
@@ -527,6 +529,19 @@ def main():
     _, _, ms_sp, prof_sp, worst_sp, sh_sp, _, lat_sp = measure(1, False)
     conv_sp = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_sp[l] == 0))
     value_sp = world * conv_sp * args.steps / (ms_sp * 1e-3)
+
+    # the comparison baseline: Henry's solve per shift, unblocked (the RQIN of
+    # the paper's experiments), FP64, same workload, same backtransform
+    bsteps = 3
+    _, _, ms_b, prof_b, worst_b, sh_b, _, lat_b = measure(0, False, method=1, steps=bsteps)
+    conv_b = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_b[l] == 0))
+    baseline = {"method": "Henry's RQ solve per shift, unblocked (one thread block per shift "
+                          "over the whole matrix), FP64; same prepare, normalization and "
+                          "z = Q0 x",
+                "value": world * conv_b * bsteps / (ms_b * 1e-3), "unit": UNIT,
+                "ms_per_step": ms_b / bsteps, "residual_max_over_n_eps": worst_b,
+                "not_converged": int((sh_b != 0).sum()),
+                "phases": {k: {"ms_per_step": v[0] / bsteps} for k, v in prof_b.items()}}
 
     if rank != 0:
         return
@@ -594,6 +609,7 @@ def main():
                            % (conv_cols, ncol),
         "restart": restart,
         "split_precision": split,
+        "per_shift_baseline": baseline,
     }
     if not args.no_batch and world == 1:
         line["batching"] = measure_batch(args, torch, hs, hi)

@@ -70,7 +70,12 @@ typedef struct {
     int omega_log2; /* stored solution entries stay below 2^omega_log2; 0 = default (1000).  */
                     /* Lower values (>= 16) make the scaling of Sec. 4.1 trigger on small     */
                     /* problems, for testing                                                 */
-    int reserved[4];
+    int method;     /* 0 = the tiled level-3 solve (default); 1 = the comparison baseline:   */
+                    /*     Henry's RQ solve per shift, unblocked (Alg. "henry", the RQIN of   */
+                    /*     Sec. 5), one thread block per shift over the whole matrix, with   */
+                    /*     the same protection, normalization and backtransform; precision  */
+                    /*     must be 0                                                         */
+    int reserved[3];
 } hsein_options;
 
 /* Fill *opt with the defaults.  Returns HSEIN_EARG for opt == NULL. */

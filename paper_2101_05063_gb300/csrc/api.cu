@@ -168,7 +168,10 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         o.precision = opt->precision;
         o.robust = opt->robust;
         if (opt->omega_log2 != 0) o.omega_log2 = opt->omega_log2;
+        o.method = opt->method;
     }
+    if (o.method != 0 && o.method != 1) return HSEIN_EARG;
+    if (o.method == 1 && o.precision != 0) return HSEIN_EARG;  // the baseline is FP64
     if (o.br < 8 || o.br > hsein::kMaxBr || o.br % 8 != 0) return HSEIN_EARG;
     if (o.precision != 0 && o.precision != 1) return HSEIN_EARG;
     if (o.precision == 1 && o.br != 64) return HSEIN_EARG;  // digit tiles are 64 wide
@@ -223,6 +226,23 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
             return HSEIN_ECUDA;
         }
         plan->maps_work = dWork;
+    }
+    if (plan->opt.method == 1) {
+        // comparison baseline: Henry's solve per shift over the whole matrix
+        {
+            PhaseScope ps(plan, 0, s);
+            hsein::launch_prepare(L, dWork, dH, ldh, dWr, dWi, dB, ldb, om, s);
+        }
+        {
+            PhaseScope ps(plan, 1, s);
+            hsein::launch_henry(L, dWork, dH, ldh, robust, om, s);
+        }
+        {
+            PhaseScope ps(plan, 3, s);
+            hsein::launch_finalize(L, dWork, dX, ldx, dStatus, s);
+        }
+        if (cudaGetLastError() != cudaSuccess) return HSEIN_ECUDA;
+        return HSEIN_OK;
     }
     {
         PhaseScope ps(plan, 0, s);

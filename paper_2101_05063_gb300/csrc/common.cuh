@@ -118,6 +118,9 @@ void launch_split_h(const Layout& L, void* work, const double* H, int ldh, cudaS
 size_t oz_update_hd_elems(const Layout& L);
 void launch_finalize(const Layout& L, void* work, double* X, int ldx, int* status,
                      cudaStream_t s);
+// comparison baseline: Henry's solve per shift, unblocked (csrc/k_henry.cu)
+void launch_henry(const Layout& L, void* work, const double* H, int ldh, int robust,
+                  int omega_log2, cudaStream_t s);
 // restart of non-converged shifts (csrc/restart.cu)
 size_t restart_scratch_bytes(int n, int k);
 void launch_restart_trial(int n, int t, int k, const int* map, const double* wr, const double* wi,
