@@ -228,6 +228,21 @@ hsein_status hsein_plan_destroy(hsein_plan_t plan);
 const char *hsein_status_string(hsein_status status);
 
 /*
+ * Householder reduction to upper Hessenberg form on the GPU: A = Q0 H Q0^T
+ * (Sec. 1: H and Q0 come from A before the solve; LAPACK's DGEHRD and
+ * DORGHR).  Step k (k = 1..n-2) applies P = I - 2 v v^T / (v^T v),
+ * v = x - alpha e_1 for x = H(k+1:n, k) and alpha = -sign(x_1) ||x||, from the
+ * left and the right and accumulates Q0 <- Q0 P; H(k+1, k) becomes alpha and
+ * H(k+2:n, k) exactly 0.  dA n x n (lda >= n, not modified); dH, dQ n x n
+ * outputs (ldh, ldq >= n; distinct from dA and from each other).  dWork of
+ * hsein_gehrd_workspace bytes, 256-byte aligned.  Stream-ordered (n - 2 steps
+ * of a few kernels each).
+ */
+hsein_status hsein_gehrd_workspace(int n, size_t *workspace_bytes);
+hsein_status hsein_gehrd(int n, const double *dA, int lda, double *dH, int ldh, double *dQ,
+                         int ldq, void *dWork, size_t work_bytes, void *stream);
+
+/*
  * Power-of-two balancing of an upper Hessenberg matrix, so that graded inputs
  * (rows and columns of very different scale) can use the split-precision
  * products: integer exponents e with Hb = D^-1 H D, D = diag(2^e) (exact:

@@ -26,7 +26,7 @@ __all__ = [
     "hsein_batch_info", "hsein_batch_destroy", "HseinInstance", "HseinBatchConfig", "Batch",
     "HseinRequest", "hsein_server_create", "hsein_server_submit", "hsein_server_progress",
     "hsein_server_stats", "hsein_server_destroy", "Server", "hsein_balance", "hsein_unbalance",
-    "balance", "unbalance",
+    "balance", "unbalance", "hsein_gehrd_workspace", "hsein_gehrd", "gehrd",
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
     "STATUS", "PHASES",
@@ -121,6 +121,10 @@ def load(build_if_missing=True):
     lib.hsein_balance.argtypes = [ip, dp, ip, dp, ip, dp, ip, vp]
     lib.hsein_unbalance.restype = ctypes.c_int
     lib.hsein_unbalance.argtypes = [ip, ip, dp, dp, dp, ip, vp]
+    lib.hsein_gehrd_workspace.restype = ctypes.c_int
+    lib.hsein_gehrd_workspace.argtypes = [ip, ctypes.POINTER(sz)]
+    lib.hsein_gehrd.restype = ctypes.c_int
+    lib.hsein_gehrd.argtypes = [ip, dp, ip, dp, ip, dp, ip, vp, sz, vp]
     lib.hsein_server_create.restype = ctypes.c_int
     lib.hsein_server_create.argtypes = [ctypes.POINTER(vp), sz, ip, ip, ctypes.POINTER(HseinOptions)]
     lib.hsein_server_submit.restype = ctypes.c_int
@@ -272,6 +276,35 @@ def unbalance(X, wi, exps):
                            _ld(X), torch.cuda.current_stream(X.device).cuda_stream),
            "hsein_unbalance")
     return X
+
+
+def hsein_gehrd_workspace(n):
+    """Returns (status, workspace bytes)."""
+    w = ctypes.c_size_t()
+    rc = load().hsein_gehrd_workspace(n, ctypes.byref(w))
+    return rc, w.value
+
+
+def hsein_gehrd(n, dA, lda, dH, ldh, dQ, ldq, dWork, work_bytes, stream):
+    return load().hsein_gehrd(n, dA, lda, dH, ldh, dQ, ldq, dWork, work_bytes, stream or None)
+
+
+def gehrd(A):
+    """Householder reduction of a CUDA float64 square matrix: returns (H, Q0)
+    with A = Q0 H Q0^T, H upper Hessenberg (exact zeros below the first
+    subdiagonal) and Q0 orthogonal, both column-major."""
+    import torch
+    A = _colmajor(A, torch)
+    n = A.shape[0]
+    H = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    Q = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    rc, wb = hsein_gehrd_workspace(n)
+    _check(rc, "hsein_gehrd_workspace")
+    work = torch.empty(wb, dtype=torch.uint8, device=A.device)
+    _check(hsein_gehrd(n, A.data_ptr(), _ld(A), H.data_ptr(), _ld(H), Q.data_ptr(), _ld(Q),
+                       work.data_ptr(), wb, torch.cuda.current_stream(A.device).cuda_stream),
+           "hsein_gehrd")
+    return H, Q
 
 
 def hsein_server_create(hbm_bytes, max_jobs, max_merge_shifts, opt=None):
