@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=4000,
                     help="requests in the serving stream (the full workload is 20000)")
     ap.add_argument("--cpu-sample", type=int, default=256, help="shifts in the oracle sample")
+    ap.add_argument("--no-reduction", action="store_true",
+                    help="skip timing the Hessenberg reduction A -> (H, Q0)")
     return ap.parse_args()
 
 
@@ -378,6 +380,43 @@ def measure_serving(args, torch, hs, hi):
             "pool": {str(n): len(v) for n, v in pool.items()}, "generation_s": t_gen}
 
 
+def measure_reduction(inst, torch, hs, fp64_peak):
+    """The precursor step A = Q0 H Q0^T (hsein_gehrd) on the workload's own A:
+    two timed calls after one warm-up (CUDA events on the calling stream),
+    with invariant checks on the device.  Algorithmic work of the level-2
+    reduction with Q0 accumulated: per step 4 m^2 (left reflection of the
+    trailing block) + 4 n m (right reflection) + 4 n m (Q0 P) flops,
+    m = n - k - 1, i.e. 16/3 n^3 in total."""
+    import numpy as np
+    n = inst.n
+    dA = torch.as_tensor(np.asfortranarray(inst.A), dtype=torch.float64, device="cuda")
+    hs.gehrd(dA)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    e0.record()
+    for _ in range(reps):
+        dH, dQ = hs.gehrd(dA)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = sum(4.0 * (n - k - 1) ** 2 + 8.0 * n * (n - k - 1) for k in range(n - 2))
+    achieved = flops / (ms * 1e-3) / 1e12
+    eye = torch.eye(n, dtype=torch.float64, device="cuda")
+    orth = float((dQ.t() @ dQ - eye).abs().max())
+    back = float((dQ @ dH @ dQ.t() - dA).abs().max()) / float(dA.abs().max())
+    lapack = float(np.abs(np.abs(dH.cpu().numpy()) - np.abs(inst.H)).max() / np.abs(inst.A).max())
+    below = int(torch.count_nonzero(torch.tril(dH, -2)))
+    return {"n": n, "ms": ms, "unit": "ms per reduction (A -> H, Q0)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                         "algorithmic_flops": flops},
+            "gpu_launches": 1 + 4 * (n - 2),
+            "checks": {"max_abs_QtQ_minus_I": orth, "max_abs_QHQt_minus_A_over_max_A": back,
+                       "max_abs_absH_minus_abs_lapack_H_over_max_A": lapack,
+                       "nonzeros_below_subdiagonal": below}}
+
+
 def workload_config(inst, br):
     return {
         "workload": "mixed real/complex shifts: n=4096, 512 real + 256 complex shifts "
@@ -400,7 +439,7 @@ def main():
 
     rank, world, local = dist_setup()
     dev = torch.device("cuda", local)
-    inst = hi.config1(seed=1 + rank)
+    inst = hi.config1(seed=1 + rank, keep_a=True)
     n, ncol, m = inst.n, inst.ncol, inst.m
     f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device=dev)
     dH, dwr, dwi, dB, dQ = f(inst.H), f(inst.wr), f(inst.wi), f(inst.B), f(inst.Q0)
@@ -611,6 +650,8 @@ def main():
         "split_precision": split,
         "per_shift_baseline": baseline,
     }
+    if not args.no_reduction and world == 1:
+        line["reduction"] = measure_reduction(inst, torch, hs, fp64_peak)
     if not args.no_batch and world == 1:
         line["batching"] = measure_batch(args, torch, hs, hi)
     if not args.no_serve and world == 1:

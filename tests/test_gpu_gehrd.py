@@ -108,12 +108,22 @@ def test_gehrd_then_solve_gives_eigenvectors_of_a():
         assert r <= 100 * inst.n * EPS, (l, r)
 
 
-def test_gehrd_full_size_properties():
-    # the n = 4096 mixed workload's A: invariants on the GPU (no oracle run)
-    inst = hi.config1(keep_a=True)
-    dA = to_dev(inst.A)
+@pytest.mark.parametrize("case", ["normal2048", "config1"])
+def test_gehrd_full_size_properties(case):
+    # sizes whose early steps take the wide tile shapes (two and four rows per
+    # thread): invariants on the GPU and |H| against LAPACK's reduction (no
+    # oracle run at these sizes)
+    import scipy.linalg
+    if case == "config1":
+        inst = hi.config1(keep_a=True)
+        A, Hs = inst.A, inst.H
+    else:
+        n = 2048
+        A = hi.normal(11, 62, n * n).reshape(n, n, order="F")
+        Hs = np.triu(scipy.linalg.hessenberg(A), -1)
+    n = A.shape[0]
+    dA = to_dev(A)
     dH, dQ = hs.gehrd(dA)
-    n = inst.n
     i, j = torch.meshgrid(torch.arange(n, device="cuda"), torch.arange(n, device="cuda"),
                           indexing="ij")
     assert bool((dH[i > j + 1] == 0).all())
@@ -122,5 +132,4 @@ def test_gehrd_full_size_properties():
     back = dQ @ dH @ dQ.t()
     assert float((back - dA).abs().max()) <= 20 * n * EPS * float(dA.abs().max()) * np.sqrt(n)
     # |H| agrees with the LAPACK reduction (unique up to reflector signs)
-    Hs = np.abs(inst.H)
-    assert np.abs(np.abs(dH.cpu().numpy()) - Hs).max() <= 1e-8 * np.abs(inst.A).max()
+    assert np.abs(np.abs(dH.cpu().numpy()) - np.abs(Hs)).max() <= 1e-8 * np.abs(A).max()
