@@ -22,6 +22,8 @@
 #include "ozaki.cuh"
 #include "tc.cuh"
 
+#include <type_traits>
+
 #include <algorithm>
 
 namespace hsein {
@@ -244,6 +246,7 @@ k_update_oz(Layout L, void* work, int J, int tiles_per_cta, const __grid_constan
         const int q = warp & 3, g = (warp - 2) >> 2;
         const int gi = m0 + 32 * q + lane;
         const bool rv = gi < p0, last = gi == p0 - 1;
+        const bool last_warp = m0 + 32 * q <= p0 - 1 && p0 - 1 < m0 + 32 * q + 32;
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
         const Epi* epi = ws<Epi>(work, L.off_epi);
         double* X = ws<double>(work, L.off_X);
@@ -287,7 +290,12 @@ k_update_oz(Layout L, void* work, int J, int tiles_per_cta, const __grid_constan
             }
             tc::tc_fence_after();
             uint32_t mb[4] = {0, 0, 0, 0}, mr[4] = {0, 0, 0, 0};
-            // two halves of 4 product columns: one pair of solution columns each
+            // two halves of 4 product columns: one pair of solution columns
+            // each.  The warp that holds row p0-1 runs its own instance with
+            // that row's constant terms; every other warp runs none of them
+            // (as selects they would cost every lane FP64 adds)
+            auto halves = [&](auto LASTc) {
+            constexpr bool LASTW = decltype(LASTc)::value;
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 uint32_t a[kS][4];
@@ -314,7 +322,7 @@ k_update_oz(Layout L, void* work, int J, int tiles_per_cta, const __grid_constan
                     double vbr = fma(ui, E.zbr_im, fma(-ur, E.zbr_re, fma(br, E.fB, -z[0])));
                     double vbi = fma(-ui, E.zbr_re, fma(-ur, E.zbr_im, fma(bi, E.fB, -z[2])));
                     double vrr = fma(E.pi, ur, z[1]), vri = fma(E.pi, ui, z[3]);
-                    if (last) {
+                    if (LASTW && last) {
                         vbr += E.cz_re;
                         vbi += E.cz_im;
                         vrr -= E.cw_re;
@@ -338,7 +346,7 @@ k_update_oz(Layout L, void* work, int J, int tiles_per_cta, const __grid_constan
                         const double u_ = rv4[2 * u + k];
                         double vb = fma(-u_, E.zbr_re, fma(xv[2 * u + k], E.fB, -z[2 * k]));
                         double vr = fma(E.pi, u_, z[2 * k + 1]);
-                        if (last) {
+                        if (LASTW && last) {
                             vb += E.cz_re;
                             vr -= E.cw_re;
                         }
@@ -349,6 +357,9 @@ k_update_oz(Layout L, void* work, int J, int tiles_per_cta, const __grid_constan
                     }
                 }
             }
+            };
+            if (last_warp) halves(std::true_type{});
+            else halves(std::false_type{});
             {
                 // per-shift maxima over the warp's 32 rows; lanes 0..7 post them
                 uint32_t mine = 0;
