@@ -541,33 +541,30 @@ def main():
     h2d = 8 * (2 * n * n + n * ncol + 2 * m)
     d2h = 8 * n * ncol + 4 * m
 
-    def e2e_step():
-        dH.copy_(hH, non_blocking=True)
-        dwr.copy_(hwr, non_blocking=True)
-        dwi.copy_(hwi, non_blocking=True)
-        dB.copy_(hB, non_blocking=True)
-        dQ.copy_(hQ, non_blocking=True)
-        step()
-        hZ.copy_(Z, non_blocking=True)
-        hS.copy_(status, non_blocking=True)
+    # the binding's end-to-end call: inputs up, solve (Q0's upload overlapped
+    # with it), backtransform, Z and the status codes down
+    def time_e2e(slv):
+        slv.solve_host(hH, hwr, hwi, hB, hQ, hZ, hS)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(args.steps):
+            slv.solve_host(hH, hwr, hwi, hB, hQ, hZ, hS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return max_over_ranks(e0.elapsed_time(e1), world)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
+    ms_e2e = time_e2e(solver)
     e2e_value = world * conv_cols * args.steps / (ms_e2e * 1e-3)
 
     # ---------------- the split-precision path on the same inputs ----------
     del solver
-    _, _, ms_sp, prof_sp, worst_sp, sh_sp, _, lat_sp = measure(1, False)
+    solver_sp, _, ms_sp, prof_sp, worst_sp, sh_sp, _, lat_sp = measure(1, False)
     conv_sp = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_sp[l] == 0))
     value_sp = world * conv_sp * args.steps / (ms_sp * 1e-3)
+    e2e_value_sp = world * conv_sp * args.steps / (time_e2e(solver_sp) * 1e-3)
+    del solver_sp
 
     # the comparison baseline: Henry's solve per shift, unblocked (the RQIN of
     # the paper's experiments), FP64, same workload, same backtransform
@@ -614,6 +611,8 @@ def main():
     split = {
         "value": value_sp, "unit": UNIT, "ms_per_step": ms_sp / args.steps, "latency": lat_sp,
         "vs_plain_fp64": value_sp / value,
+        "e2e": {"value": e2e_value_sp, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "vs_plain_fp64_e2e": e2e_value_sp / e2e_value},
         "residual_max_over_n_eps": worst_sp, "not_converged": int((sh_sp != 0).sum()),
         "phases": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                    for k, v in prof_sp.items()},

@@ -492,6 +492,45 @@ class Solver:
                "hsein_margins")
         return out
 
+    def solve_host(self, hH, hwr, hwi, hB, hQ0, hZ, hstatus):
+        """End to end from host memory: H, the shifts and B go to the device
+        first; Q0 follows on a second stream while the solve runs (it is
+        needed only by the backtransform); Z = Q0 X and the status codes come
+        back into hZ and hstatus.  Host tensors should be pinned and laid out
+        like the device operands (column-major).  Stream-ordered on the
+        current stream: synchronize before reading hZ and hstatus.  Device
+        buffers are allocated on the first call and reused."""
+        torch = self.torch
+        st = torch.cuda.current_stream(self.device)
+        if getattr(self, "_e2e", None) is None:
+            mk = lambda r, c: torch.empty((c, r), dtype=torch.float64, device=self.device).t()
+            self._e2e = {"H": mk(self.n, self.n), "Q": mk(self.n, self.n),
+                         "B": mk(self.n, self.ncol), "X": mk(self.n, self.ncol),
+                         "Z": mk(self.n, self.ncol),
+                         "wr": torch.empty(self.m, dtype=torch.float64, device=self.device),
+                         "wi": torch.empty(self.m, dtype=torch.float64, device=self.device),
+                         "status": torch.empty(self.m, dtype=torch.int32, device=self.device),
+                         "side": torch.cuda.Stream(self.device)}
+        d = self._e2e
+        d["H"].copy_(hH, non_blocking=True)
+        d["wr"].copy_(hwr, non_blocking=True)
+        d["wi"].copy_(hwi, non_blocking=True)
+        if hB is not None:
+            d["B"].copy_(hB, non_blocking=True)
+        # Q0 after the solve's own inputs (they share the link) and after the
+        # previous call's backtransform has read the buffer
+        side = d["side"]
+        side.wait_stream(st)
+        with torch.cuda.stream(side):
+            d["Q"].copy_(hQ0, non_blocking=True)
+        X, status = self.solve(d["H"], d["wr"], d["wi"], d["B"] if hB is not None else None,
+                               X=d["X"], status=d["status"], check=False)
+        st.wait_stream(side)
+        Z = self.backtransform(d["Q"], X, d["Z"])
+        hZ.copy_(Z, non_blocking=True)
+        hstatus.copy_(status, non_blocking=True)
+        return hZ, hstatus
+
     def backtransform(self, Q0, X, Z=None):
         """Z = Q0 X (eigenvectors of A = Q0 H Q0^T)."""
         torch = self.torch

@@ -310,3 +310,23 @@ def test_split_precision_bad_system_h2(n, om):
     assert sg[0] == 0 and so[0] == 0 and np.all(np.isfinite(Xg))
     assert angle(Xg[:, 0], Xo[:, 0]) <= 1e-12
     assert residual(H, 2.0, Xg[:, 0]) <= 100 * n * EPS
+
+
+def test_solve_host_matches_device_path():
+    # the end-to-end call from pinned host buffers gives the device path's
+    # results bit for bit (same kernels on the same inputs), twice in a row
+    inst = hi.small_instance(300, 9, 5, 44)
+    n, ncol, m = inst.n, inst.ncol, inst.m
+    s = hs.Solver(n, inst.m_real, inst.m_cplx)
+    X, st = s.solve(to_dev(inst.H), to_dev(inst.wr), to_dev(inst.wi), to_dev(inst.B))
+    Z = s.backtransform(to_dev(inst.Q0), X).cpu().numpy()
+    st = st.cpu().numpy()
+    pin = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64).pin_memory()
+    hZ = torch.empty((ncol, n), dtype=torch.float64).pin_memory().t()
+    hS = torch.empty(m, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        hZ.zero_()
+        s.solve_host(pin(inst.H), pin(inst.wr), pin(inst.wi), pin(inst.B), pin(inst.Q0), hZ, hS)
+        torch.cuda.synchronize()
+        assert np.array_equal(hZ.numpy(), Z)
+        assert np.array_equal(hS.numpy(), st)
