@@ -98,6 +98,23 @@ __device__ inline double bits_to_double(unsigned long long b) {
     return __longlong_as_double((long long)b);
 }
 
+// |v| as an order-preserving integer: the bit pattern without the sign
+__device__ inline unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+}
+
+// 2^d exactly (from the exponent field where 2^d is normal)
+__device__ inline double pow2(int d) {
+    if (d >= -1022 && d <= 1023) return __longlong_as_double((long long)(d + 1023) << 52);
+    return ldexp(1.0, d);
+}
+
+// exponent of the scale 2^e for a norm whose largest magnitude has the bit
+// pattern mbits: 2^e <= max < 2^(e+1), e kept above -1020 so 2^-e is finite
+__device__ inline int norm_exp(unsigned long long mbits) {
+    return mbits == 0 ? 0 : max(ilogb(bits_to_double(mbits)), -1020);
+}
+
 __device__ inline void set_error(DevState* st, int code) {
     atomicMin(&st->status, code);
 }

@@ -3,8 +3,9 @@
 //
 //  1. alpha_min: the largest tile exponent e_max; every tile segment is
 //     brought to it by an exact power-of-two factor (consistency scaling).
-//  2. DNRM2-style scaled 2-norm (running maximum and scaled sum), reduced
-//     across the block in a fixed tree order.
+//  2. Scaled 2-norm: the largest magnitude (integer maximum of the bit
+//     patterns), then the sum of squares scaled by its power of two, reduced
+//     across the block in a fixed order.
 //  3. Varah's test: ||x||_2 2^e_max / ||b||_2 > 1 / (10 n ||H||_inf eps),
 //     evaluated in log2.  A column that fails is set to zero (Sec. 4.2).
 //  4. y = G_n^H (... (G_2^H (x / ||x||))): the recurrence
@@ -19,34 +20,6 @@ namespace hsein {
 namespace {
 
 constexpr int kThreads = 256;
-
-struct Nrm {
-    double m, t;
-};
-__device__ inline Nrm nrm_add(Nrm a, double v) {
-    double x = fabs(v);
-    if (x == 0.0) return a;
-    if (a.m < x) {
-        double r = a.m / x;
-        a.t = 1.0 + a.t * r * r;
-        a.m = x;
-    } else {
-        double r = x / a.m;
-        a.t += r * r;
-    }
-    return a;
-}
-__device__ inline Nrm nrm_merge(Nrm a, Nrm b) {
-    if (a.m < b.m) {
-        Nrm t = a;
-        a = b;
-        b = t;
-    }
-    if (a.m == 0.0) return a;
-    double r = b.m / a.m;
-    a.t += b.t * r * r;
-    return a;
-}
 
 // affine map tau -> a tau + (br + i bi), a real
 struct Aff {
@@ -71,7 +44,8 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
     const double* Ci = ws<double>(work, L.off_Ci);
     const double* Sv = ws<double>(work, L.off_S);
     __shared__ int s_emax;
-    __shared__ double s_m[32], s_t[32];
+    __shared__ unsigned long long s_mb[32];
+    __shared__ double s_t[32];
     __shared__ Aff s_aff[32];
     __shared__ int s_conv;
     __shared__ double s_scale;
@@ -94,30 +68,45 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
     // tile of row i and its consistency factor 2^(e_tile - e_max)
     auto factor = [&](int i) {
         int J = i < L.b0 ? 0 : 1 + (i - L.b0) / L.br;
-        return ldexp(1.0, etile[(size_t)J * L.m + q] - emax);
+        return pow2(etile[(size_t)J * L.m + q] - emax);
     };
     const int cs = (n + kThreads - 1) / kThreads;
     const int a0 = min(n, tid * cs), a1 = min(n, a0 + cs);
-    Nrm nr{0.0, 0.0};
+    // scaled 2-norm of the consistently scaled column: the largest magnitude
+    // as an integer maximum of bit patterns, then sum (v_i 2^-e)^2 with the
+    // exact power-of-two scale 2^e of that maximum (no division per element)
+    unsigned long long mb = 0;
     for (int i = a0; i < a1; ++i) {
-        double f = factor(i);
-        nr = nrm_add(nr, xr[i] * f);
-        if (CPLX) nr = nrm_add(nr, xi[i] * f);
+        const double f = factor(i);
+        mb = max(mb, abs_bits(xr[i] * f));
+        if (CPLX) mb = max(mb, abs_bits(xi[i] * f));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Nrm other{__shfl_xor_sync(0xffffffffu, nr.m, o), __shfl_xor_sync(0xffffffffu, nr.t, o)};
-        nr = nrm_merge(nr, other);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if (lane == 0) s_mb[warp] = mb;
+    __syncthreads();
+    mb = s_mb[0];
+    for (int w = 1; w < kThreads / 32; ++w) mb = max(mb, s_mb[w]);
+    const int ne = norm_exp(mb);
+    const double nsc = pow2(-ne);
+    double ss = 0.0;
+    for (int i = a0; i < a1; ++i) {
+        const double g = factor(i) * nsc;
+        const double t0 = xr[i] * g;
+        ss = fma(t0, t0, ss);
+        if (CPLX) {
+            const double t1 = xi[i] * g;
+            ss = fma(t1, t1, ss);
+        }
     }
-    if (lane == 0) {
-        s_m[warp] = nr.m;
-        s_t[warp] = nr.t;
-    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) s_t[warp] = ss;
     __syncthreads();
     if (tid == 0) {
-        Nrm a{0.0, 0.0};
-        for (int w = 0; w < kThreads / 32; ++w) a = nrm_merge(a, Nrm{s_m[w], s_t[w]});
-        const double nrm = a.m * sqrt(a.t);
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += s_t[w];
+        const double nrm = mb == 0 ? 0.0 : sqrt(t) * pow2(ne);
         const double thr = -log2(10.0 * n * st->hnorm * 0x1p-53);
         const double margin = nrm > 0.0 ? log2(nrm) + emax - log2(bnorm[q]) - thr : -HUGE_VAL;
         int conv = margin > 0.0;

@@ -178,35 +178,6 @@ __global__ void k_rownorm(Layout L, void* work, int row_blocks) {
     }
 }
 
-// DNRM2-style partial (xmax, t): the norm is xmax * sqrt(t)
-struct Nrm {
-    double m, t;
-};
-__device__ inline Nrm nrm_add(Nrm a, double v) {
-    double x = fabs(v);
-    if (x == 0.0) return a;
-    if (a.m < x) {
-        double r = a.m / x;
-        a.t = 1.0 + a.t * r * r;
-        a.m = x;
-    } else {
-        double r = x / a.m;
-        a.t += r * r;
-    }
-    return a;
-}
-__device__ inline Nrm nrm_merge(Nrm a, Nrm b) {
-    if (a.m < b.m) {
-        Nrm t = a;
-        a = b;
-        b = t;
-    }
-    if (a.m == 0.0) return a;
-    double r = b.m / a.m;
-    a.t += b.t * r * r;
-    return a;
-}
-
 __global__ void k_init(Layout L, void* work, const double* __restrict__ H, int ldh,
                        const double* __restrict__ wr, const double* __restrict__ wi,
                        const double* __restrict__ B, int ldb) {
@@ -245,58 +216,68 @@ __global__ void k_init(Layout L, void* work, const double* __restrict__ H, int l
     const int c = qcolumn(L, q);
     const int uc = qcol[q];
     const double rho = kEps * hn;  // default starting vector rho*e (Sec. 4.2)
-    Nrm nb{0.0, 0.0};
-    double xm = 0.0, rm = 0.0;
+    // pass 1: X = B, R~ = h(:, n) - lambda e_n, and the largest magnitudes
+    // (integer maxima of the bit patterns: no FP64 work)
+    unsigned long long xm = 0, rm = 0;
     for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-        double b0 = B ? B[i + (size_t)uc * ldb] : rho;
-        double b1 = cplx ? (B ? B[i + (size_t)(uc + 1) * ldb] : 0.0) : 0.0;
+        const double b0 = B ? B[i + (size_t)uc * ldb] : rho;
         X[i + (size_t)c * L.ldw] = b0;
-        nb = nrm_add(nb, b0);
-        xm = fmax(xm, fabs(b0));
-        double r0 = H[i + (size_t)(L.n - 1) * ldh] * hscale - (i == L.n - 1 ? lre : 0.0);
+        xm = max(xm, abs_bits(b0));
+        const double r0 = H[i + (size_t)(L.n - 1) * ldh] * hscale - (i == L.n - 1 ? lre : 0.0);
         R[i + (size_t)c * L.ldw] = r0;
-        rm = fmax(rm, fabs(r0));
+        rm = max(rm, abs_bits(r0));
         if (cplx) {
+            const double b1 = B ? B[i + (size_t)(uc + 1) * ldb] : 0.0;
             X[i + (size_t)(c + 1) * L.ldw] = b1;
-            nb = nrm_add(nb, b1);
-            xm = fmax(xm, fabs(b1));
-            double r1 = (i == L.n - 1) ? -lim : 0.0;
+            xm = max(xm, abs_bits(b1));
+            const double r1 = (i == L.n - 1) ? -lim : 0.0;
             R[i + (size_t)(c + 1) * L.ldw] = r1;
-            rm = fmax(rm, fabs(r1));
+            rm = max(rm, abs_bits(r1));
         }
     }
-    __shared__ double s_m[32], s_t[32], s_x[32], s_r[32];
+    __shared__ unsigned long long s_x[32], s_r[32];
+    __shared__ double s_t[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        Nrm other{__shfl_xor_sync(0xffffffffu, nb.m, o), __shfl_xor_sync(0xffffffffu, nb.t, o)};
-        nb = nrm_merge(nb, other);
-        xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
-        rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+        xm = max(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+        rm = max(rm, __shfl_xor_sync(0xffffffffu, rm, o));
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        s_m[warp] = nb.m;
-        s_t[warp] = nb.t;
         s_x[warp] = xm;
         s_r[warp] = rm;
     }
     __syncthreads();
-    if (warp == 0) {
-        int nw = blockDim.x >> 5;
-        Nrm a{lane < nw ? s_m[lane] : 0.0, lane < nw ? s_t[lane] : 0.0};
-        double x = lane < nw ? s_x[lane] : 0.0, r = lane < nw ? s_r[lane] : 0.0;
+    xm = s_x[0];
+    rm = s_r[0];
+    for (int w = 1; w < nw; ++w) {
+        xm = max(xm, s_x[w]);
+        rm = max(rm, s_r[w]);
+    }
+    // pass 2: ||b||_2 = 2^e sqrt(sum (b_i 2^-e)^2), 2^e the scale of the
+    // largest |b_i| (exact power-of-two scaling; the column is re-read from
+    // cache)
+    const int e = norm_exp(xm);
+    const double sc = pow2(-e);
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+        const double t0 = X[i + (size_t)c * L.ldw] * sc;
+        ss = fma(t0, t0, ss);
+        if (cplx) {
+            const double t1 = X[i + (size_t)(c + 1) * L.ldw] * sc;
+            ss = fma(t1, t1, ss);
+        }
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            Nrm other{__shfl_xor_sync(0xffffffffu, a.m, o), __shfl_xor_sync(0xffffffffu, a.t, o)};
-            a = nrm_merge(a, other);
-            x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-            r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-        }
-        if (lane == 0) {
-            bnorm[q] = a.m * sqrt(a.t);
-            bmax[q] = (unsigned long long)__double_as_longlong(x);
-            rmax[q] = (unsigned long long)__double_as_longlong(r);
-        }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) s_t[warp] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += s_t[w];
+        bnorm[q] = xm == 0 ? 0.0 : sqrt(t) * pow2(e);
+        bmax[q] = xm;
+        rmax[q] = rm;
     }
 }
 
