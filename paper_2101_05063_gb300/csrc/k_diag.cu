@@ -97,7 +97,8 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
     double* Sv = ws<double>(work, L.off_S);
     double* ZW = ws<double>(work, L.off_ZW);
 
-    // per-group shared scratch: c (re, im), s, x (re, im), shifted diagonal
+    // per-group shared scratch: c (re, im), s, x (re, im), shifted diagonal,
+    // squared subdiagonal
     double* s_cr = sm;
     double* s_ci = sm + br;
     double* s_s = sm + 2 * br;
@@ -157,8 +158,10 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
     // when any group needs the overflow scaling of phi or a protection step
     // (ProtectDivision / ProtectUpdate), the whole warp recomputes the step
     // the careful way, which gives the same values whenever nothing rescales.
-    double* s_d = sm + 5 * br;  // h(i,i) - Re(lambda): the shifted diagonal
+    double* s_d = sm + 5 * br;   // h(i,i) - Re(lambda): the shifted diagonal
+    double* s_h2 = sm + 6 * br;  // h(k,k-1)^2, the rotation's constant term
     for (int i = r; i + 1 < bt; i += LPS) s_d[i] = Hs[(i + 1) * br + i] - lre;
+    for (int k = r; k < bt; k += LPS) s_h2[k] = Hs[(size_t)k * br + k] * Hs[(size_t)k * br + k];
     __syncwarp();
     const int role = r;
     // the rotation waiting for the slots below the pivot slot (identity at first)
@@ -201,7 +204,8 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
         apply_pending(std::integral_constant<int, TK>{});
 
         // rotation (eq. "givens" / "cgivens"): 1/phi = rsqrt(h^2 + |v|^2)
-        const double ss = CPLX ? fma(vkr, vkr, fma(vki, vki, hs * hs)) : fma(vkr, vkr, hs * hs);
+        const double h2 = s_h2[k];
+        const double ss = CPLX ? fma(vkr, vkr, fma(vki, vki, h2)) : fma(vkr, vkr, h2);
         const double rr = rsqrt(ss);
         double m1;
         if (CPLX)
@@ -659,13 +663,13 @@ k_diag(Layout L, void* work, int J, int robust, int om, int nbc) {
         constexpr int G = 32 / LPSC;
         const int g = lane / LPSC;
         const int q = G * b + g;
-        double* scratch = smem + (size_t)br * br + (size_t)g * 6 * br;
+        double* scratch = smem + (size_t)br * br + (size_t)g * 7 * br;
         tile_group<LPSC, RPLC, true>(L, work, Hs, J, p0, bt, q, q < L.mc, robust, om, scratch);
     } else {
         constexpr int G = 32 / LPSR;
         const int g = lane / LPSR;
         const int q = L.mc + G * (b - nbc) + g;
-        double* scratch = smem + (size_t)br * br + (size_t)g * 6 * br;
+        double* scratch = smem + (size_t)br * br + (size_t)g * 7 * br;
         tile_group<LPSR, RPLR, false>(L, work, Hs, J, p0, bt, q, q < L.m, robust, om, scratch);
     }
 }
@@ -715,7 +719,7 @@ static void launch_t(const Layout& L, void* work, int J, int robust, int om, int
 }
 
 static size_t diag_smem(int br) {
-    return ((size_t)br * br + (size_t)kMaxGroups * 6 * br) * sizeof(double);
+    return ((size_t)br * br + (size_t)kMaxGroups * 7 * br) * sizeof(double);
 }
 
 void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, int robust,
