@@ -123,18 +123,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend="nccl"):
+    """Rank, world size and local rank from the launcher's environment; joins
+    the process group when there is more than one rank (NCCL on GPUs; gloo for
+    host-only runs).  Each rank drives its own GPU."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if backend == "nccl":
+        torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(local)
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return rank, world, local
+
+
+def _reduce(v, world, op, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
 
 
 def barrier(world):
@@ -143,14 +158,22 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
-    if world == 1:
-        return v
-    import torch
+def max_over_ranks(v, world, device="cuda"):
+    """The slowest rank's time: the whole job is done when it is."""
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _reduce(v, world, dist.ReduceOp.MAX if world > 1 else None, device)
+
+
+def sum_over_ranks(v, world, device="cuda"):
+    """Units processed by all ranks together (each rank solves its own
+    seeded instance, so their converged-column counts may differ)."""
+    import torch.distributed as dist
+    return _reduce(v, world, dist.ReduceOp.SUM if world > 1 else None, device)
+
+
+def rank_seed(rank):
+    """Seed of the instance a rank solves (weak scaling: one instance per rank)."""
+    return 1 + rank
 
 
 def update_flops(n, ncol, br):
@@ -439,7 +462,7 @@ def main():
 
     rank, world, local = dist_setup()
     dev = torch.device("cuda", local)
-    inst = hi.config1(seed=1 + rank, keep_a=True)
+    inst = hi.config1(seed=rank_seed(rank), keep_a=True)
     n, ncol, m = inst.n, inst.ncol, inst.m
     f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device=dev)
     dH, dwr, dwi, dB, dQ = f(inst.H), f(inst.wr), f(inst.wi), f(inst.B), f(inst.Q0)
@@ -514,7 +537,8 @@ def main():
     solver, step, ms, prof, worst, sh, clocks, lat = measure(0, True)
     # eigenvectors that pass Varah's test (the others are zeroed columns)
     conv_cols = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh[l] == 0))
-    value = world * conv_cols * args.steps / (ms * 1e-3)
+    all_cols = sum_over_ranks(conv_cols, world)
+    value = all_cols * args.steps / (ms * 1e-3)
 
     # restart (Alg. "hsrq3in") of the shifts that did not converge, timed once
     # after a fresh solve: the cost of making every column converge
@@ -528,7 +552,7 @@ def main():
     conv_r = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_r[l] == 0))
     restart = {"retried_shifts": n_retried, "not_converged_after": int((sh_r != 0).sum()),
                "ms": ms_restart, "clock": "host wall time (the restart synchronizes)",
-               "value_with_restart": world * conv_r / ((ms / args.steps + ms_restart) * 1e-3),
+               "value_with_restart": sum_over_ranks(conv_r, world) / ((ms / args.steps + ms_restart) * 1e-3),
                "unit": UNIT}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -556,14 +580,15 @@ def main():
         return max_over_ranks(e0.elapsed_time(e1), world)
 
     ms_e2e = time_e2e(solver)
-    e2e_value = world * conv_cols * args.steps / (ms_e2e * 1e-3)
+    e2e_value = all_cols * args.steps / (ms_e2e * 1e-3)
 
     # ---------------- the split-precision path on the same inputs ----------
     del solver
     solver_sp, _, ms_sp, prof_sp, worst_sp, sh_sp, _, lat_sp = measure(1, False)
     conv_sp = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_sp[l] == 0))
-    value_sp = world * conv_sp * args.steps / (ms_sp * 1e-3)
-    e2e_value_sp = world * conv_sp * args.steps / (time_e2e(solver_sp) * 1e-3)
+    all_sp = sum_over_ranks(conv_sp, world)
+    value_sp = all_sp * args.steps / (ms_sp * 1e-3)
+    e2e_value_sp = all_sp * args.steps / (time_e2e(solver_sp) * 1e-3)
     del solver_sp
 
     # the comparison baseline: Henry's solve per shift, unblocked (the RQIN of
@@ -574,7 +599,7 @@ def main():
     baseline = {"method": "Henry's RQ solve per shift, unblocked (one thread block per shift "
                           "over the whole matrix), FP64; same prepare, normalization and "
                           "z = Q0 x",
-                "value": world * conv_b * bsteps / (ms_b * 1e-3), "unit": UNIT,
+                "value": sum_over_ranks(conv_b, world) * bsteps / (ms_b * 1e-3), "unit": UNIT,
                 "ms_per_step": ms_b / bsteps, "residual_max_over_n_eps": worst_b,
                 "not_converged": int((sh_b != 0).sum()),
                 "phases": {k: {"ms_per_step": v[0] / bsteps} for k, v in prof_b.items()}}
