@@ -188,6 +188,24 @@ def update_flops(n, ncol, br):
     return total, N - 1
 
 
+def diag_flops(inst, br):
+    """Algorithmic flops of all diagonal-tile sweeps of one solve (k_diag, one
+    launch per tile).  Per shift and tile of height bt: the row updates of the
+    sweep, bt(bt-1)/2 rows of x -= a v - b t, v = c t + s v (7 flops real, 18
+    complex), a rotation with its division per step (10 / 20 flops), and the
+    Z'/W build (12 / 24 flops per row)."""
+    n = inst.n
+    N = (n + br - 1) // br
+    b0 = n - (N - 1) * br
+    total = 0
+    for J in range(N):
+        bt = b0 if J == 0 else br
+        rows = bt * (bt - 1) // 2
+        total += inst.m_real * (7 * rows + 10 * (bt - 1) + 12 * bt)
+        total += inst.m_cplx * (18 * rows + 20 * (bt - 1) + 24 * bt)
+    return total, N
+
+
 def source_hash(relpath):
     with open(os.path.join(ROOT, relpath), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -534,29 +552,6 @@ def main():
         clocks = sampler.stop() if sampler else None
         return solver, step, max_over_ranks(ms, world), prof, worst, sh, clocks, lat
 
-    solver, step, ms, prof, worst, sh, clocks, lat = measure(0, True)
-    # eigenvectors that pass Varah's test (the others are zeroed columns)
-    conv_cols = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh[l] == 0))
-    all_cols = sum_over_ranks(conv_cols, world)
-    value = all_cols * args.steps / (ms * 1e-3)
-
-    # restart (Alg. "hsrq3in") of the shifts that did not converge, timed once
-    # after a fresh solve: the cost of making every column converge
-    step()
-    torch.cuda.synchronize()
-    r0 = time.perf_counter()
-    rc_r, n_retried = solver.restart(dH, dwr, dwi, X, status, B=dB, max_tries=3)
-    torch.cuda.synchronize()
-    ms_restart = (time.perf_counter() - r0) * 1e3
-    sh_r = status.cpu().numpy()
-    conv_r = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_r[l] == 0))
-    restart = {"retried_shifts": n_retried, "not_converged_after": int((sh_r != 0).sum()),
-               "ms": ms_restart, "clock": "host wall time (the restart synchronizes)",
-               "value_with_restart": sum_over_ranks(conv_r, world) / ((ms / args.steps + ms_restart) * 1e-3),
-               "unit": UNIT}
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-
     # ---------------- end to end through the API with host buffers ---------
     pin = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64).pin_memory()
     hH, hwr, hwi, hB, hQ = pin(inst.H), pin(inst.wr), pin(inst.wi), pin(inst.B), pin(inst.Q0)
@@ -564,6 +559,8 @@ def main():
     hS = torch.empty(m, dtype=torch.int32).pin_memory()
     h2d = 8 * (2 * n * n + n * ncol + 2 * m)
     d2h = 8 * n * ncol + 4 * m
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
 
     # the binding's end-to-end call: inputs up, solve (Q0's upload overlapped
     # with it), backtransform, Z and the status codes down
@@ -579,23 +576,47 @@ def main():
         barrier(world)
         return max_over_ranks(e0.elapsed_time(e1), world)
 
-    ms_e2e = time_e2e(solver)
-    e2e_value = all_cols * args.steps / (ms_e2e * 1e-3)
+    def converged_columns(sh_):
+        # eigenvectors that pass Varah's test (the others are zeroed columns)
+        return int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_[l] == 0))
 
-    # ---------------- the split-precision path on the same inputs ----------
+    # ---------------- the plain FP64 path (the metric's comparison) --------
+    solver, step, ms, prof, worst, sh, clocks, lat = measure(0, True)
+    conv_cols = converged_columns(sh)
+    all_cols = sum_over_ranks(conv_cols, world)
+    value = all_cols * args.steps / (ms * 1e-3)
+    e2e_value = all_cols * args.steps / (time_e2e(solver) * 1e-3)
     del solver
-    solver_sp, _, ms_sp, prof_sp, worst_sp, sh_sp, _, lat_sp = measure(1, False)
-    conv_sp = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_sp[l] == 0))
+
+    # ---------------- the split-precision path: the headline ---------------
+    solver_sp, step_sp, ms_sp, prof_sp, worst_sp, sh_sp, clocks_sp, lat_sp = measure(1, True)
+    conv_sp = converged_columns(sh_sp)
     all_sp = sum_over_ranks(conv_sp, world)
     value_sp = all_sp * args.steps / (ms_sp * 1e-3)
     e2e_value_sp = all_sp * args.steps / (time_e2e(solver_sp) * 1e-3)
+
+    # restart (Alg. "hsrq3in") of the shifts that did not converge, timed once
+    # after a fresh solve: the cost of making every column converge
+    step_sp()
+    torch.cuda.synchronize()
+    r0 = time.perf_counter()
+    rc_r, n_retried = solver_sp.restart(dH, dwr, dwi, X, status, B=dB, max_tries=3)
+    torch.cuda.synchronize()
+    ms_restart = (time.perf_counter() - r0) * 1e3
+    sh_r = status.cpu().numpy()
+    conv_r = converged_columns(sh_r)
+    restart = {"retried_shifts": n_retried, "not_converged_after": int((sh_r != 0).sum()),
+               "ms": ms_restart, "clock": "host wall time (the restart synchronizes)",
+               "value_with_restart": sum_over_ranks(conv_r, world)
+               / ((ms_sp / args.steps + ms_restart) * 1e-3),
+               "unit": UNIT}
     del solver_sp
 
     # the comparison baseline: Henry's solve per shift, unblocked (the RQIN of
     # the paper's experiments), FP64, same workload, same backtransform
     bsteps = 3
     _, _, ms_b, prof_b, worst_b, sh_b, _, lat_b = measure(0, False, method=1, steps=bsteps)
-    conv_b = int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_b[l] == 0))
+    conv_b = converged_columns(sh_b)
     baseline = {"method": "Henry's RQ solve per shift, unblocked (one thread block per shift "
                           "over the whole matrix), FP64; same prepare, normalization and "
                           "z = Q0 x",
@@ -608,70 +629,87 @@ def main():
         return
     pk, pk_kind = peaks()
     fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16  # TFLOP/s
+    peak_source = ("FP64: %s bf16 %.1f TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
+                   % (pk_kind, pk["bf16_tflops"]))
     uf, ulaunch = update_flops(n, ncol, args.br)
     q0f = 2.0 * n * n * ncol
-    phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-              for k, v in prof.items()}
-    dominant = max(prof, key=lambda k: prof[k][0])
-    if dominant == "q0_backtransform":
-        flops_launch, t_launch = q0f, prof[dominant][0] / max(1, prof[dominant][1])
-        kfile, summary = "paper_2101_05063_gb300/csrc/k_q0.cu", "k_q0_config1.txt"
-        kname = "k_q0"
+    per_phase = lambda pr: {k: {"ms_per_step": v[0] / args.steps,
+                                "launches_per_step": v[1] / args.steps} for k, v in pr.items()}
+
+    # plain FP64 path: its dominant kernel is the shared-H product k_update
+    # (or z = Q0 x when that takes longer)
+    if max(prof, key=lambda k: prof[k][0]) == "q0_backtransform":
+        flops_launch = q0f
+        t_launch = prof["q0_backtransform"][0] / max(1, prof["q0_backtransform"][1])
+        kfile, summary, kname = "paper_2101_05063_gb300/csrc/k_q0.cu", "k_q0_config1.txt", "k_q0"
     else:
         flops_launch = uf / ulaunch
         t_launch = prof["shared_h_update"][0] / max(1, prof["shared_h_update"][1])
-        kfile, summary = "paper_2101_05063_gb300/csrc/k_update.cu", "k_update_config1.txt"
-        kname = "k_update"
-        dominant = "shared_h_update"
+        kfile, summary, kname = ("paper_2101_05063_gb300/csrc/k_update.cu",
+                                 "k_update_config1.txt", "k_update")
     achieved = flops_launch / (t_launch * 1e-3) / 1e12
     # prepare is five kernels (setup, row sums, tile norms, init, tile
-    # staging); the other phases are one kernel per recorded launch
+    # staging), six in split mode (+ the digit split of H); z = Q0 x is four
+    # in split mode (row maxima, two splits, the product); the other phases
+    # are one kernel per recorded launch
     launches = 5 * prof["prepare"][1] + sum(v[1] for k, v in prof.items() if k != "prepare")
-    # split mode: the digit products run on the BF16 tensor cores; 28 digit
+    launches_sp = (6 * prof_sp["prepare"][1] + 4 * prof_sp["q0_backtransform"][1]
+                   + sum(v[1] for k, v in prof_sp.items()
+                         if k not in ("prepare", "q0_backtransform")))
+    plain = {
+        "value": value, "unit": UNIT, "ms_per_step": ms / args.steps, "latency": lat,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "residual_max_over_n_eps": worst, "not_converged": int((sh != 0).sum()),
+        "phases": per_phase(prof), "gpu_launches": launches, "clocks": clocks, "dtype": "f64",
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "traffic": profiled_traffic(kfile, summary), "peak_source": peak_source,
+                     "algorithmic_flops_per_launch": flops_launch},
+    }
+
+    # split path: the digit products run on the BF16 tensor cores; 28 digit
     # pairs per product (7 digits, pairs above the FP64 rounding level)
     t_upd_sp = prof_sp["shared_h_update"][0] / args.steps
     t_q0_sp = prof_sp["q0_backtransform"][0] / args.steps
     tensor_upd = 28.0 * uf / (t_upd_sp * 1e-3) / 1e12
     tensor_q0 = 28.0 * q0f / (t_q0_sp * 1e-3) / 1e12
-    split = {
-        "value": value_sp, "unit": UNIT, "ms_per_step": ms_sp / args.steps, "latency": lat_sp,
-        "vs_plain_fp64": value_sp / value,
-        "e2e": {"value": e2e_value_sp, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "vs_plain_fp64_e2e": e2e_value_sp / e2e_value},
-        "residual_max_over_n_eps": worst_sp, "not_converged": int((sh_sp != 0).sum()),
-        "phases": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-                   for k, v in prof_sp.items()},
-        "tensor": {"peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                   "shared_h_update_achieved": tensor_upd,
-                   "shared_h_update_frac": tensor_upd / pk["bf16_tflops"],
-                   "q0_backtransform_achieved": tensor_q0,
-                   "q0_backtransform_frac": tensor_q0 / pk["bf16_tflops"],
-                   "engine": "tcgen05.mma kind::f16 (bf16 x bf16 -> fp32 in TMEM), TMA-staged tiles"},
-        "dtype": "f64 results; bf16 digit products with exact integer accumulation",
-    }
+    tensor = {"peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+              "shared_h_update_achieved": tensor_upd,
+              "shared_h_update_frac": tensor_upd / pk["bf16_tflops"],
+              "q0_backtransform_achieved": tensor_q0,
+              "q0_backtransform_frac": tensor_q0 / pk["bf16_tflops"],
+              "engine": "tcgen05.mma kind::f16 (bf16 x bf16 -> fp32 in TMEM), TMA-staged tiles"}
+    # the split path's dominant kernel: the diagonal-tile sweep k_diag (FP64)
+    df, dlaunch = diag_flops(inst, args.br)
+    t_diag = prof_sp["diag_sweep"][0] / max(1, prof_sp["diag_sweep"][1])
+    achieved_d = df / dlaunch / (t_diag * 1e-3) / 1e12
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "latency": lat,
+        "metric": METRIC, "value": value_sp, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_sp / args.steps, "latency": lat_sp,
         "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (bf16 digit-sliced products)", "data": "synthetic",
         "config": workload_config(inst, args.br),
-        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved,
-                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "traffic": profiled_traffic(kfile, summary),
-                     "peak_source": "FP64: %s bf16 %.1f TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
-                                    % (pk_kind, pk["bf16_tflops"]),
-                     "algorithmic_flops_per_launch": flops_launch},
-        "phases": phases,
-        "residual_max_over_n_eps": worst,
-        "not_converged": int((sh != 0).sum()),
-        "clocks": clocks,
-        "gpu_launches": launches,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "vs_plain_fp64_gpu": value_sp / value,
+        "roofline": {"kernel": "k_diag", "bound": "alu", "achieved": achieved_d,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_d / fp64_peak,
+                     "traffic": profiled_traffic("paper_2101_05063_gb300/csrc/k_diag.cu",
+                                                 "k_diag_config1.txt"),
+                     "peak_source": peak_source,
+                     "algorithmic_flops_per_launch": df / dlaunch},
+        "tensor": tensor,
+        "phases": per_phase(prof_sp),
+        "residual_max_over_n_eps": worst_sp,
+        "not_converged": int((sh_sp != 0).sum()),
+        "clocks": clocks_sp,
+        "gpu_launches": launches_sp,
+        "e2e": {"value": e2e_value_sp, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "vs_plain_fp64_gpu_e2e": e2e_value_sp / e2e_value},
         "columns_counted": "converged columns only (%d of %d); complex shifts count 2"
-                           % (conv_cols, ncol),
+                           % (conv_sp, ncol),
         "restart": restart,
-        "split_precision": split,
+        "plain_fp64": plain,
         "per_shift_baseline": baseline,
     }
     if not args.no_reduction and world == 1:
