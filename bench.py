@@ -461,9 +461,10 @@ def measure_reduction(inst, torch, hs, fp64_peak):
 def workload_config(inst, br):
     return {
         "workload": "mixed real/complex shifts: n=4096, 512 real + 256 complex shifts "
-                    "(1024 columns), FP64 products, tile height %d" % br,
+                    "(1024 columns), split-precision products (BF16 digit slices on the "
+                    "tensor cores; plain_fp64: FP64 products), tile height %d" % br,
         "n": inst.n, "m_real": inst.m_real, "m_cplx": inst.m_cplx, "columns": inst.ncol,
-        "br": br, "precision": "fp64",
+        "br": br, "precision": "split (plain_fp64: fp64)",
         "l2": "no flush: H and Q0 (134 MB each) are larger than L2",
     }
 
