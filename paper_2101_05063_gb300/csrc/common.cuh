@@ -109,6 +109,13 @@ __device__ inline double pow2(int d) {
     return ldexp(1.0, d);
 }
 
+// 2^d for -1074 <= d <= 1023 from the bit pattern alone (normal and
+// subnormal powers of two), no library call
+__device__ inline double exact_pow2(int d) {
+    return d >= -1022 ? __longlong_as_double((long long)(d + 1023) << 52)
+                      : __longlong_as_double(1LL << (d + 1074));
+}
+
 // exponent of the scale 2^e for a norm whose largest magnitude has the bit
 // pattern mbits: 2^e <= max < 2^(e+1), e kept above -1020 so 2^-e is finite
 __device__ inline int norm_exp(unsigned long long mbits) {

@@ -248,7 +248,7 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
             // overflow, then the protections with rescaling of x
             double hsc = hs, vsr = vkr, vsi = vki, sc = 1.0;
             if (eh > 500 || eh < -500) {
-                sc = scalbn(1.0, -eh);
+                sc = exact_pow2(min(-eh, 1023));  // eh in [-1073, 1024]: 2^-eh, finite
                 hsc *= sc;
                 vsr *= sc;
                 if (CPLX) vsi *= sc;
@@ -359,7 +359,7 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
             int eh = max(lbound(hs), lbound(vsr));
             if (CPLX) eh = max(eh, lbound(vsi));
             if (eh > 500 || eh < -500) {
-                sc = scalbn(1.0, -eh);
+                sc = exact_pow2(min(-eh, 1023));  // eh in [-1073, 1024]: 2^-eh, finite
                 hs *= sc;
                 vsr *= sc;
                 vsi *= sc;
