@@ -692,7 +692,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 (bf16 digit-sliced products)", "data": "synthetic",
         "config": workload_config(inst, args.br),
-        "vs_plain_fp64_gpu": value_sp / value,
+        "vs_plain_fp64_gpu": value_sp / value if value > 0 else None,
         "roofline": {"kernel": "k_diag", "bound": "alu", "achieved": achieved_d,
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_d / fp64_peak,
                      "traffic": profiled_traffic("paper_2101_05063_gb300/csrc/k_diag.cu",
@@ -706,7 +706,8 @@ def main():
         "clocks": clocks_sp,
         "gpu_launches": launches_sp,
         "e2e": {"value": e2e_value_sp, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "vs_plain_fp64_gpu_e2e": e2e_value_sp / e2e_value},
+                "d2h_bytes_per_step": d2h,
+                "vs_plain_fp64_gpu_e2e": e2e_value_sp / e2e_value if e2e_value > 0 else None},
         "columns_counted": "converged columns only (%d of %d); complex shifts count 2"
                            % (conv_sp, ncol),
         "restart": restart,
