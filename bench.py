@@ -510,12 +510,12 @@ def main():
             worst = max(worst, np.abs(hx - lam * x).sum() / (hn1 * np.abs(x).sum()))
         return worst / (n * EPS)
 
-    def measure(precision, sample_clocks, method=0, steps=None):
+    def measure(precision, sample_clocks, method=0, steps=None, givens=0):
         """Warm up, check, then time `steps` (default args.steps) steps of one
-        precision mode / method."""
+        precision mode / method / rotation storage."""
         nsteps = steps or args.steps
         solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=args.br, precision=precision,
-                           device=dev, method=method)
+                           device=dev, method=method, givens=givens)
 
         def step():
             solver.solve(dH, dwr, dwi, dB, X=X, status=status, check=False)
@@ -612,6 +612,18 @@ def main():
                / ((ms_sp / args.steps + ms_restart) * 1e-3),
                "unit": UNIT}
     del solver_sp
+
+    # the headline path with the rotations stored compactly (Sec. 4.4)
+    solver_c, _, ms_c, prof_c, worst_c, sh_c, _, lat_c = measure(1, False, givens=1, steps=5)
+    compact = {"value": sum_over_ranks(converged_columns(sh_c), world) * 5 / (ms_c * 1e-3),
+               "unit": UNIT, "ms_per_step": ms_c / 5, "residual_max_over_n_eps": worst_c,
+               "not_converged": int((sh_c != 0).sum()),
+               "workspace_bytes_saved": None,
+               "phases": {k: {"ms_per_step": v[0] / 5} for k, v in prof_c.items()}}
+    compact["workspace_bytes_saved"] = (
+        hs.Solver(n, inst.m_real, inst.m_cplx, br=args.br, precision=1, device=dev).work_bytes
+        - solver_c.work_bytes)
+    del solver_c
 
     # the comparison baseline: Henry's solve per shift, unblocked (the RQIN of
     # the paper's experiments), FP64, same workload, same backtransform
@@ -713,6 +725,7 @@ def main():
         "restart": restart,
         "plain_fp64": plain,
         "per_shift_baseline": baseline,
+        "compact_givens": compact,
     }
     if not args.no_reduction and world == 1:
         line["reduction"] = measure_reduction(inst, torch, hs, fp64_peak)

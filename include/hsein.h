@@ -75,7 +75,13 @@ typedef struct {
                     /*     Sec. 5), one thread block per shift over the whole matrix, with   */
                     /*     the same protection, normalization and backtransform; precision  */
                     /*     must be 0                                                         */
-    int reserved[3];
+    int givens;     /* storage of the Givens rotations between the solve and its            */
+                    /*     backtransform: 0 = c and s as computed (default); 1 = compact     */
+                    /*     (Sec. 4.4, Stewart's scheme): one number per real rotation, two   */
+                    /*     per complex rotation, the other quantities recomputed with a      */
+                    /*     square root from c^2 + s^2 = 1; saves n x (m_real + m_cplx)       */
+                    /*     doubles of workspace.  method must be 0                           */
+    int reserved[2];
 } hsein_options;
 
 /* Fill *opt with the defaults.  Returns HSEIN_EARG for opt == NULL. */

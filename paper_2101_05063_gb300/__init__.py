@@ -48,7 +48,7 @@ class HseinError(RuntimeError):
 class HseinOptions(ctypes.Structure):
     _fields_ = [("br", ctypes.c_int), ("precision", ctypes.c_int), ("robust", ctypes.c_int),
                 ("omega_log2", ctypes.c_int), ("method", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("givens", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class HseinInstance(ctypes.Structure):
@@ -412,7 +412,7 @@ class Solver:
     """
 
     def __init__(self, n, m_real, m_cplx, br=64, robust=True, omega_log2=1000, precision=0,
-                 device=None, method=0):
+                 device=None, method=0, givens=0):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -423,6 +423,7 @@ class Solver:
             opt.omega_log2 = int(omega_log2)
             opt.precision = int(precision)
             opt.method = int(method)
+            opt.givens = int(givens)
             self.plan, self.work_bytes = hsein_plan(n, m_real, m_cplx, opt)
         self.n, self.m_real, self.m_cplx = int(n), int(m_real), int(m_cplx)
         self.m = self.m_real + self.m_cplx

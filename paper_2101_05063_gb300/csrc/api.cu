@@ -50,7 +50,7 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-void make_layout(Layout* L, int n, int mr, int mc, int br, int precision) {
+void make_layout(Layout* L, int n, int mr, int mc, int br, int precision, int givens) {
     L->n = n;
     L->mr = mr;
     L->mc = mc;
@@ -84,7 +84,8 @@ void make_layout(Layout* L, int n, int mr, int mc, int br, int precision) {
     L->off_R = take(sizeof(double) * (size_t)L->ldw * L->ncolp);
     L->off_Cr = take(sizeof(double) * nn * m);
     L->off_Ci = take(sizeof(double) * nn * (size_t)(mc > 0 ? mc : 1));
-    L->off_S = take(sizeof(double) * nn * m);
+    L->compact = givens;
+    L->off_S = take(givens ? 0 : sizeof(double) * nn * m);  // compact: no separate s
     L->off_ZW = take(sizeof(double) * (size_t)br * 2 * L->ncolp);
     L->off_dt = take(sizeof(double) * N * br * br);
     L->off_margin = take(sizeof(double) * m);
@@ -169,9 +170,12 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         o.robust = opt->robust;
         if (opt->omega_log2 != 0) o.omega_log2 = opt->omega_log2;
         o.method = opt->method;
+        o.givens = opt->givens;
     }
     if (o.method != 0 && o.method != 1) return HSEIN_EARG;
     if (o.method == 1 && o.precision != 0) return HSEIN_EARG;  // the baseline is FP64
+    if (o.givens != 0 && o.givens != 1) return HSEIN_EARG;
+    if (o.givens == 1 && o.method != 0) return HSEIN_EARG;  // the baseline stores c and s
     if (o.br < 8 || o.br > hsein::kMaxBr || o.br % 8 != 0) return HSEIN_EARG;
     if (o.precision != 0 && o.precision != 1) return HSEIN_EARG;
     if (o.precision == 1 && o.br != 64) return HSEIN_EARG;  // digit tiles are 64 wide
@@ -179,7 +183,7 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
     if (o.omega_log2 < 16 || o.omega_log2 > 1000) return HSEIN_EARG;
     hsein_plan_s* p = new (std::nothrow) hsein_plan_s;
     if (!p) return HSEIN_ENOMEM;
-    make_layout(&p->L, n, m_real, m_cplx, o.br, o.precision);
+    make_layout(&p->L, n, m_real, m_cplx, o.br, o.precision, o.givens);
     p->opt = o;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||

@@ -63,7 +63,8 @@ struct Layout {
     size_t off_state, off_qsrc, off_qcol, off_lam, off_bnorm, off_eB, off_etile, off_bmax,
         off_rmax, off_epi, off_anorm, off_rowpart, off_X, off_R, off_Cr, off_Ci, off_S, off_ZW,
         off_dt, off_hd, off_he, off_zwd, off_zwf, off_margin, off_oz, total;
-    int oz;  // 1: split-precision shared-H update (BF16 digits), 0: FP64
+    int oz;       // 1: split-precision shared-H update (BF16 digits), 0: FP64
+    int compact;  // 1: Givens rotations stored compactly (Stewart's scheme)
 };
 
 // first row of tile J (tile 0 is the ragged top-left tile of height b0)
@@ -114,6 +115,104 @@ __device__ inline double pow2(int d) {
 __device__ inline double exact_pow2(int d) {
     return d >= -1022 ? __longlong_as_double((long long)(d + 1023) << 52)
                       : __longlong_as_double(1LL << (d + 1074));
+}
+
+// ---- Givens rotations: canonical sign and compact storage (Sec. 4.4) ----
+// A rotation (c, s) and its negation (-c, -s) (with phi -> -phi and
+// x(k) -> -x(k)) serve the solve equally well; the solution of
+// (H - lambda I) x = b is the same.  With compact storage the sweep keeps
+// the canonical one:
+// real rotations have the larger of |c|, |s| positive, complex rotations
+// (c complex, s real) have s >= 0.  Stewart's compact storage recovers
+// exactly the canonical rotation: it keeps the smaller quantity (halved)
+// or twice the reciprocal of the larger one, and recomputes the other from
+// c^2 + s^2 = 1 by a well-conditioned square root.
+
+constexpr unsigned long long kSignBit = 0x8000000000000000ULL;
+
+__device__ inline double flip_if(double v, unsigned long long f) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)f);
+}
+
+// sign-bit mask that makes the rotation canonical (0: keep it)
+template <bool CPLX>
+__device__ inline unsigned long long canon_mask(double cr, double ci, double s) {
+    (void)ci;
+    const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
+    if (CPLX) return sb & kSignBit;  // s >= 0
+    const unsigned long long cb = (unsigned long long)__double_as_longlong(cr);
+    return (sb & ~kSignBit) < (cb & ~kSignBit) ? (cb & kSignBit) : (sb & kSignBit);
+}
+
+// one number for a canonical real rotation: s/2 (|s| < |c|, c > 0; |value|
+// < 0.36), 1 (c = 0, s = 1), or 2/c (|c| <= |s|, s > 0; |value| >= 2.8)
+__device__ inline double givens_pack_real(double c, double s) {
+    if (fabs(s) < fabs(c)) return 0.5 * s;
+    return c == 0.0 ? 1.0 : 2.0 / c;
+}
+__device__ inline void givens_unpack_real(double r, double& c, double& s) {
+    if (r == 1.0) {
+        c = 0.0;
+        s = 1.0;
+    } else if (fabs(r) < 1.0) {
+        s = 2.0 * r;
+        c = sqrt(fma(-s, s, 1.0));
+    } else {
+        c = 2.0 / r;
+        s = sqrt(fma(-c, c, 1.0));
+    }
+}
+
+// two numbers for a canonical complex rotation (s >= 0): the first encodes
+// (|c|, s) as above with the sign of Re c in its sign bit, the second the
+// direction c/|c| taken with Re >= 0 (encoded like a real rotation, with
+// +-1 for a purely imaginary direction), 0 when c = 0
+__device__ inline void givens_pack_cplx(double cr, double ci, double s, double& r1, double& r2) {
+    const double a = sqrt(fma(cr, cr, ci * ci));
+    const double e = s < a ? 0.5 * s : (a == 0.0 ? 1.0 : 2.0 / a);
+    r1 = copysign(e, cr);
+    if (a == 0.0) {
+        r2 = 0.0;
+        return;
+    }
+    const double wr = fabs(cr) / a, wi = copysign(1.0, cr) * ci / a;  // w = sign(Re c) c / |c|
+    if (fabs(wi) < wr) r2 = 0.5 * wi;
+    else r2 = wr == 0.0 ? (wi > 0.0 ? 1.0 : -1.0) : copysign(2.0 / wr, wi);
+}
+__device__ inline void givens_unpack_cplx(double r1, double r2, double& cr, double& ci,
+                                          double& s) {
+    const double r = fabs(r1);
+    double a;
+    if (r == 1.0) {
+        a = 0.0;
+        s = 1.0;
+    } else if (r < 1.0) {
+        s = 2.0 * r;
+        a = sqrt(fma(-s, s, 1.0));
+    } else {
+        a = 2.0 / r;
+        s = sqrt(fma(-a, a, 1.0));
+    }
+    if (a == 0.0) {
+        cr = 0.0;
+        ci = 0.0;
+        return;
+    }
+    double wr, wi;
+    const double q = fabs(r2);
+    if (q == 1.0) {
+        wr = 0.0;
+        wi = r2;
+    } else if (q < 1.0) {
+        wi = 2.0 * r2;
+        wr = sqrt(fma(-wi, wi, 1.0));
+    } else {
+        wr = 2.0 / q;
+        wi = copysign(sqrt(fma(-wr, wr, 1.0)), r2);
+    }
+    const double g = copysign(a, r1);  // c = sign(Re c) |c| w
+    cr = g * wr;
+    ci = g * wi;
 }
 
 // exponent of the scale 2^e for a norm whose largest magnitude has the bit

@@ -295,6 +295,16 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
             bx = nb;
         }
 
+        if (L.compact) {
+            // the canonical rotation (what compact storage recovers); a and b
+            // do not change with the flip
+            const unsigned long long f = canon_mask<CPLX>(cr, ci, s);
+            cr = flip_if(cr, f);
+            ci = flip_if(ci, f);
+            s = flip_if(s, f);
+            xkr1 = flip_if(xkr1, f);
+            xki1 = flip_if(xki1, f);
+        }
         // row k is final
         if (r == rk) {
             xr[TK] = xkr1;
@@ -376,6 +386,14 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
             }
             x0r *= rinv;
             x0i *= rinv;
+            if (L.compact) {
+                const unsigned long long f = canon_mask<CPLX>(c0r, c0i, s0);
+                c0r = flip_if(c0r, f);
+                c0i = flip_if(c0i, f);
+                s0 = flip_if(s0, f);
+                x0r = flip_if(x0r, f);
+                x0i = flip_if(x0i, f);
+            }
         } else {
             c0r = 1.0;
             c0i = 0.0;
@@ -443,9 +461,14 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
     if (qok) {
         for (int i = r; i < bt; i += LPS) {
             const size_t gi = (size_t)q * L.n + p0 + i;
-            Cr[gi] = s_cr[i];
-            Sv[gi] = s_s[i];
-            if (CPLX) Ci[gi] = s_ci[i];
+            if (L.compact) {  // Stewart's storage (Sec. 4.4)
+                if (CPLX) givens_pack_cplx(s_cr[i], s_ci[i], s_s[i], Cr[gi], Ci[gi]);
+                else Cr[gi] = givens_pack_real(s_cr[i], s_s[i]);
+            } else {
+                Cr[gi] = s_cr[i];
+                Sv[gi] = s_s[i];
+                if (CPLX) Ci[gi] = s_ci[i];
+            }
         }
         if (r == 0) etile[(size_t)J * L.m + q] = e;
     }

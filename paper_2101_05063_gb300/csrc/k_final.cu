@@ -56,7 +56,22 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
     const double* xi = X + (size_t)(col + 1) * L.ldw;
     const double* cr = Cr + (size_t)q * n;
     const double* ci = Ci + (size_t)q * n;
-    const double* sv = Sv + (size_t)q * n;
+    const double* sv = Sv + (size_t)q * n;  // not read with compact storage
+    // rotation k as stored by the sweep (compact: Stewart's scheme, Sec. 4.4)
+    auto rot = [&](int k, double& c_r, double& c_i, double& s_) {
+        if (L.compact) {
+            if (CPLX) {
+                givens_unpack_cplx(cr[k], ci[k], c_r, c_i, s_);
+            } else {
+                givens_unpack_real(cr[k], c_r, s_);
+                c_i = 0.0;
+            }
+        } else {
+            c_r = cr[k];
+            c_i = CPLX ? ci[k] : 0.0;
+            s_ = sv[k];
+        }
+    };
 
     if (tid == 0) {
         int em = etile[q];
@@ -139,7 +154,8 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
         if (k == 0) {
             step = Aff{0.0, yk_r, yk_i};
         } else {
-            double c_r = cr[k], c_i = CPLX ? ci[k] : 0.0, s = sv[k];
+            double c_r, c_i, s;
+            rot(k, c_r, c_i, s);
             // conj(c) y
             step = Aff{s, c_r * yk_r + c_i * yk_i, c_r * yk_i - c_i * yk_r};
         }
@@ -178,7 +194,8 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
             ti = yk_i;
             continue;
         }
-        double c_r = cr[k], c_i = CPLX ? ci[k] : 0.0, s = sv[k];
+        double c_r, c_i, s;
+        rot(k, c_r, c_i, s);
         // y(k-1) = c tau - s y_k
         double outr = c_r * tr - c_i * ti - s * yk_r;
         double outi = c_r * ti + c_i * tr - s * yk_i;
