@@ -7,9 +7,18 @@ kernels of the library.  PyTorch provides device memory and streams.  There
 is no CPU fallback: if the library cannot be loaded, every call raises.
 
     import torch, paper_2101_05063_gb300 as hs
+    H, Q0 = hs.gehrd(A)                               # A = Q0 H Q0^T on the GPU
     solver = hs.Solver(n, m_real, m_cplx)             # plan + workspace
     X, status = solver.solve(H, wr, wi, B)            # unit eigenvectors of H
     Z = solver.backtransform(Q0, X)                   # eigenvectors of A
+    solver.solve_host(hH, hwr, hwi, hB, hQ0, hZ, hs)  # the same from pinned host buffers
+
+Options of Solver: precision=1 (split-precision products on the BF16 tensor
+cores, the fast mode), givens=1 (compact rotation storage), method=1 (the
+per-shift baseline), br (tile height), robust, omega_log2.  Batch runs many
+independent instances in one captured graph; Server admits requests by HBM
+footprint and fuses those on the same matrix; balance/unbalance prepare
+graded matrices for the split-precision mode.
 
 Column layout (as in the C ABI): a real shift owns one column, a complex
 shift two adjacent columns [re, im], in the input order of the shifts.
