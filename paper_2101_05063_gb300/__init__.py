@@ -11,7 +11,7 @@ is no CPU fallback: if the library cannot be loaded, every call raises.
     solver = hs.Solver(n, m_real, m_cplx)             # plan + workspace
     X, status = solver.solve(H, wr, wi, B)            # unit eigenvectors of H
     Z = solver.backtransform(Q0, X)                   # eigenvectors of A
-    solver.solve_host(hH, hwr, hwi, hB, hQ0, hZ, hs)  # the same from pinned host buffers
+    solver.solve_host(hH, hwr, hwi, hB, hQ0, hZ, hst) # the same from pinned host buffers
 
 Options of Solver: precision=1 (split-precision products on the BF16 tensor
 cores, the fast mode), givens=1 (compact rotation storage), method=1 (the
