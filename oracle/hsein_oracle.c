@@ -25,7 +25,7 @@
  * There are no tiles here: the tiled algorithm equals Henry's algorithm in
  * exact arithmetic (end of Sec. 3.2), so the untiled form is the definition.
  *
- * Readings of passages the paper leaves open (each also listed in the design doc):
+ * Readings of passages the paper leaves open:
  *  - Givens sign: phi = +sqrt(h^2 + |v|^2) > 0, c = v/phi, s = -h/phi.
  *  - ProtectUpdate / ProtectDivision are cited but not printed (Sec. 4.1);
  *    the formulas below are derived from the no-overflow requirement with

@@ -39,10 +39,14 @@ MUTANTS = {
                             "int conv = (nrm > 0.0) && (log2(nrm) - e - log2(b2) > log2_thresh);"),
     "starting_vector_rho": ("const double rho = ORACLE_EPS * hnorm;", "const double rho = 1.0 / (ORACLE_EPS * hnorm);"),
     "final_pivot_dropped": ("    x[0] /= r11;\n", "\n"),
+    "hnorm_column_sums": ("for (int j = j0; j < n; ++j) s += fabs(H[i + (size_t)j * ldh]);",
+                          "for (int j = j0; j < n; ++j) s += fabs(H[j + (size_t)i * ldh]);"),
+    "hnorm_subdiagonal_dropped": ("int j0 = i > 0 ? i - 1 : 0;", "int j0 = i;"),
 }
 
 # pin tests (function, args) run against each mutant
 PIN_CALLS = [
+    (pins.test_hnorm_inf_is_the_maximum_absolute_row_sum, ()),
     (pins.test_real_solve_matches_exact_rational, (8, 1)),
     (pins.test_real_solve_matches_exact_rational, (3, 2)),
     (pins.test_complex_solve_matches_exact_rational, (5, 4)),

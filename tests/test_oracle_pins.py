@@ -36,6 +36,27 @@ def solve_oracle_cplx(H, lam, b, **kw):
     return oracle.backtransform_cplx(C, S, x) * 2.0 ** e
 
 
+# ------------------------------------------------------------ the norm
+
+def test_hnorm_inf_is_the_maximum_absolute_row_sum():
+    # ||H||_inf sets rho = eps ||H||_inf, the pivot replacement and Varah's
+    # threshold.  A hand-computed case where the largest row sum (12, row 2,
+    # which needs its subdiagonal entry) differs from the largest column sum
+    # (11) and from the largest row sum without subdiagonal entries (6)
+    H = np.array([[1.0, -2.0, 3.0], [-10.0, 1.0, 1.0], [0.0, 1.0, -1.0]])
+    assert oracle.hnorm_inf(H) == 12.0
+    assert np.abs(H).sum(axis=0).max() == 11.0
+    # non-symmetric random Hessenberg matrices against numpy's matrix norm,
+    # with rows and columns of different scales
+    for n, seed in ((2, 1), (7, 2), (64, 3), (300, 4)):
+        H = random_hessenberg(n, seed)
+        H = H * (2.0 ** np.arange(n))[:, None] / (3.0 ** np.arange(n) / 3.0 ** n)[None, :]
+        H = np.asfortranarray(H)
+        ref = np.linalg.norm(H, np.inf)
+        assert abs(oracle.hnorm_inf(H) - ref) <= 2 * n * EPS * ref, (n, oracle.hnorm_inf(H), ref)
+        assert abs(np.abs(H).sum(axis=0).max() - ref) > 1e-3 * ref  # the test tells them apart
+
+
 # ------------------------------------------------------------ exact solves
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12])
