@@ -50,6 +50,8 @@ typedef enum {
     HSEIN_ENOTUNREDUCED = -3, /* device: some subdiagonal entry h(k,k-1) is zero          */
     HSEIN_ENONFINITE = -4,    /* device: H or a shift contains Inf or NaN                 */
     HSEIN_ECUDA = -5,         /* a CUDA call or kernel launch failed                      */
+    HSEIN_ETIMEOUT = -6,      /* device: a bounded wait of a kernel ran out (see          */
+                              /* hsein_options.wait_limit_cycles)                          */
     HSEIN_ESHIFTS = -7,       /* device: the number of wi != 0 differs from m_cplx        */
     HSEIN_WNOTCONVERGED = 1   /* device: some column failed Varah's test (zeroed)         */
 } hsein_status;
@@ -81,7 +83,13 @@ typedef struct {
                     /*     per complex rotation, the other quantities recomputed with a      */
                     /*     square root from c^2 + s^2 = 1; saves n x (m_real + m_cplx)       */
                     /*     doubles of workspace.  method must be 0                           */
-    int reserved[2];
+    long long wait_limit_cycles;
+                    /* bound of the wait of the diagonal-tile kernel for the bulk copy of   */
+                    /*     its tile (SM clock cycles from the copy's issue); when it runs    */
+                    /*     out the kernel records HSEIN_ETIMEOUT, still waits (bounded) for  */
+                    /*     the copy in flight, and returns; the solve's statuses become      */
+                    /*     HSEIN_COL_INVALID.  0 = default (2^32, about two seconds);        */
+                    /*     small values make the limit expire on purpose, for testing        */
 } hsein_options;
 
 /* Fill *opt with the defaults.  Returns HSEIN_EARG for opt == NULL. */
@@ -123,15 +131,17 @@ hsein_status hsein_solve(hsein_plan_t plan, const double *dH, int ldh,
 
 /*
  * hsein_solve without a workspace argument, for callers that cannot allocate
- * device memory (code running during CUDA stream capture, plug-ins whose host
- * framework owns all device memory, real-time paths that must not allocate).
+ * device memory (plug-ins whose host framework owns all device memory and
+ * forbids raw cudaMalloc, real-time paths that must not call an allocator).
  * The paper has no counterpart: this is an interface convenience.
  *   The workspace is a fixed 16 MiB array in the library's device memory,
  *   present on every device that loads the library until the process exits.
  *   Plans whose workspace (hsein_plan's *workspace_bytes) exceeds 16 MiB are
  *   rejected with HSEIN_ENOMEM; nothing is allocated, here or later.
- *   The first call on a device looks up the array's device address (no
- *   allocation); make that first call before any stream capture on the device.
+ *   The call runs on the current device, which must be the plan's device
+ *   (HSEIN_EARG otherwise).  The first call on a device looks up the array's
+ *   device address (no allocation) and caches it; the cache does not survive
+ *   cudaDeviceReset, so do not use this call across a reset.
  *   All calls share the array: the solve re-initializes every value it reads,
  *   but calls whose work overlaps on the GPU (other streams, other threads)
  *   race and must be serialized by the caller.  Device-side errors show in
@@ -222,6 +232,18 @@ hsein_status hsein_plan_sync_status(hsein_plan_t plan, const void *dWork, void *
 hsein_status hsein_plan_set_profiling(hsein_plan_t plan, int enable);
 hsein_status hsein_plan_profile(hsein_plan_t plan, double *ms, int *launches, int nphases,
                                 int reset);
+
+/*
+ * Measurement helper, outside the method (the paper has no counterpart): the
+ * FP64 rate of the GPU's CUDA cores, the denominator of the FP64 rooflines.
+ * Launches count threads (a multiple of 256, at most 2^31), each running
+ * eight independent chains of iters fused multiply-adds, and writes one
+ * double per thread to dOut (count entries, device).  *flops (may be NULL)
+ * receives the launch's flop count, 16 * iters * count; time the launch with
+ * events on `stream`.  Stream-ordered.
+ */
+hsein_status hsein_fp64_rate(long long iters, double *dOut, long long count, double *flops,
+                             void *stream);
 
 /* Query the plan's sizes; any output pointer may be NULL. */
 hsein_status hsein_plan_info(hsein_plan_t plan, int *n, int *m_real, int *m_cplx,

@@ -38,11 +38,12 @@ __all__ = [
     "balance", "unbalance", "hsein_gehrd_workspace", "hsein_gehrd", "gehrd",
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
-    "STATUS", "PHASES",
+    "STATUS", "PHASES", "hsein_fp64_rate", "fp64_rate",
 ]
 
 STATUS = {0: "HSEIN_OK", -1: "HSEIN_EARG", -2: "HSEIN_ENOMEM", -3: "HSEIN_ENOTUNREDUCED",
-          -4: "HSEIN_ENONFINITE", -5: "HSEIN_ECUDA", -7: "HSEIN_ESHIFTS", 1: "HSEIN_WNOTCONVERGED"}
+          -4: "HSEIN_ENONFINITE", -5: "HSEIN_ECUDA", -6: "HSEIN_ETIMEOUT", -7: "HSEIN_ESHIFTS",
+          1: "HSEIN_WNOTCONVERGED"}
 
 
 class HseinError(RuntimeError):
@@ -57,7 +58,7 @@ class HseinError(RuntimeError):
 class HseinOptions(ctypes.Structure):
     _fields_ = [("br", ctypes.c_int), ("precision", ctypes.c_int), ("robust", ctypes.c_int),
                 ("omega_log2", ctypes.c_int), ("method", ctypes.c_int),
-                ("givens", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("givens", ctypes.c_int), ("wait_limit_cycles", ctypes.c_longlong)]
 
 
 class HseinInstance(ctypes.Structure):
@@ -134,6 +135,9 @@ def load(build_if_missing=True):
     lib.hsein_gehrd_workspace.argtypes = [ip, ctypes.POINTER(sz)]
     lib.hsein_gehrd.restype = ctypes.c_int
     lib.hsein_gehrd.argtypes = [ip, dp, ip, dp, ip, dp, ip, vp, sz, vp]
+    lib.hsein_fp64_rate.restype = ctypes.c_int
+    lib.hsein_fp64_rate.argtypes = [ctypes.c_longlong, dp, ctypes.c_longlong,
+                                    ctypes.POINTER(ctypes.c_double), vp]
     lib.hsein_server_create.restype = ctypes.c_int
     lib.hsein_server_create.argtypes = [ctypes.POINTER(vp), sz, ip, ip, ctypes.POINTER(HseinOptions)]
     lib.hsein_server_submit.restype = ctypes.c_int
@@ -354,6 +358,36 @@ def hsein_server_destroy(server):
     return load().hsein_server_destroy(server)
 
 
+def hsein_fp64_rate(iters, dOut, count, stream):
+    """Launch the FP64 rate probe; returns its flop count."""
+    f = ctypes.c_double()
+    _check(load().hsein_fp64_rate(int(iters), dOut, int(count), ctypes.byref(f), stream),
+           "hsein_fp64_rate")
+    return f.value
+
+
+def fp64_rate(iters=200000, repeats=5, device=None):
+    """FP64 FMA rate of the current GPU in TFLOP/s (median over repeats of
+    one probe launch timed with CUDA events), and the per-repeat values."""
+    import torch
+    dev = torch.device(device or "cuda")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    count = sms * 1024
+    out = torch.empty(count, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    hsein_fp64_rate(1000, out.data_ptr(), count, st.cuda_stream)  # warm-up
+    vals = []
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        flops = hsein_fp64_rate(iters, out.data_ptr(), count, st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        vals.append(flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    vals.sort()
+    return vals[len(vals) // 2], vals
+
+
 def hsein_plan_info(plan):
     vals = [ctypes.c_int() for _ in range(5)]
     w = ctypes.c_size_t()
@@ -421,7 +455,7 @@ class Solver:
     """
 
     def __init__(self, n, m_real, m_cplx, br=64, robust=True, omega_log2=1000, precision=0,
-                 device=None, method=0, givens=0):
+                 device=None, method=0, givens=0, wait_limit_cycles=0):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -433,6 +467,7 @@ class Solver:
             opt.precision = int(precision)
             opt.method = int(method)
             opt.givens = int(givens)
+            opt.wait_limit_cycles = int(wait_limit_cycles)
             self.plan, self.work_bytes = hsein_plan(n, m_real, m_cplx, opt)
         self.n, self.m_real, self.m_cplx = int(n), int(m_real), int(m_cplx)
         self.m = self.m_real + self.m_cplx

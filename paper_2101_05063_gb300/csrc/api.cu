@@ -144,6 +144,11 @@ struct PhaseScope {
 
 }  // namespace
 
+namespace hsein {
+// the device a plan was created on (the device whose kernel settings it made)
+int plan_device(const hsein_plan_s* p) { return p->device; }
+}  // namespace hsein
+
 extern "C" {
 
 hsein_status hsein_default_options(hsein_options* opt) {
@@ -153,6 +158,7 @@ hsein_status hsein_default_options(hsein_options* opt) {
     opt->precision = 0;
     opt->robust = 1;
     opt->omega_log2 = 1000;
+    opt->wait_limit_cycles = 1LL << 32;
     return HSEIN_OK;
 }
 
@@ -171,7 +177,9 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         if (opt->omega_log2 != 0) o.omega_log2 = opt->omega_log2;
         o.method = opt->method;
         o.givens = opt->givens;
+        if (opt->wait_limit_cycles != 0) o.wait_limit_cycles = opt->wait_limit_cycles;
     }
+    if (o.wait_limit_cycles < 1 || o.wait_limit_cycles > (1LL << 60)) return HSEIN_EARG;
     if (o.method != 0 && o.method != 1) return HSEIN_EARG;
     if (o.method == 1 && o.precision != 0) return HSEIN_EARG;  // the baseline is FP64
     if (o.givens != 0 && o.givens != 1) return HSEIN_EARG;
@@ -257,7 +265,7 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
     for (int J = L.N - 1; J >= 1; --J) {
         {
             PhaseScope ps(plan, 1, s);
-            hsein::launch_diag(L, dWork, dH, ldh, J, robust, om, s);
+            hsein::launch_diag(L, dWork, J, robust, om, plan->opt.wait_limit_cycles, s);
         }
         PhaseScope ps(plan, 2, s);
         if (L.oz)
@@ -267,7 +275,7 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
     }
     {
         PhaseScope ps(plan, 1, s);
-        hsein::launch_diag(L, dWork, dH, ldh, 0, robust, om, s);
+        hsein::launch_diag(L, dWork, 0, robust, om, plan->opt.wait_limit_cycles, s);
     }
     {
         PhaseScope ps(plan, 3, s);
@@ -492,6 +500,7 @@ const char* hsein_status_string(hsein_status status) {
         case HSEIN_ENOTUNREDUCED: return "H is reduced: a subdiagonal entry is zero";
         case HSEIN_ENONFINITE: return "H or a shift is not finite";
         case HSEIN_ECUDA: return "CUDA error";
+        case HSEIN_ETIMEOUT: return "a bounded wait on the device ran out";
         case HSEIN_ESHIFTS: return "number of complex shifts differs from the plan";
         case HSEIN_WNOTCONVERGED: return "some columns did not converge (set to zero)";
     }

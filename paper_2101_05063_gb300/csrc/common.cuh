@@ -228,8 +228,8 @@ __device__ inline void set_error(DevState* st, int code) {
 // host launchers (one per translation unit)
 void launch_prepare(const Layout& L, void* work, const double* H, int ldh, const double* wr,
                     const double* wi, const double* B, int ldb, int omega_log2, cudaStream_t s);
-void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, int robust,
-                 int omega_log2, cudaStream_t s);
+void launch_diag(const Layout& L, void* work, int J, int robust, int omega_log2,
+                 long long wait_limit, cudaStream_t s);
 void launch_update(const Layout& L, void* work, const double* H, int ldh, int J, cudaStream_t s);
 // split-precision update: tensor maps of the A_J digit blocks (mapsA[1..N-1])
 // and of the [Z'|W] digits for the workspace at `work`

@@ -45,7 +45,10 @@ namespace hsein {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr long long kWaitLimit = 1LL << 26;  // bounded mbarrier wait (iterations)
+// after a wait has run out, the tile copy in flight still lands in this
+// block's shared memory: the block waits up to this many more cycles for it
+// before it returns
+constexpr long long kDrainCycles = 1LL << 32;
 
 // floor(log2|v|) + 1 (v < 2^L) from the exponent bits; kNegInfLog for 0
 __device__ inline int lbound(double v) {
@@ -640,7 +643,7 @@ __device__ inline uint32_t smem_u32(const void* p) {
 
 template <int LPSC, int RPLC, int LPSR, int RPLR>
 __global__ void __launch_bounds__(32)
-k_diag(Layout L, void* work, int J, int robust, int om, int nbc) {
+k_diag(Layout L, void* work, int J, int robust, int om, int nbc, long long wait_limit) {
     extern __shared__ __align__(128) double smem[];
     __shared__ __align__(8) unsigned long long mbar;
     DevState* st = ws<DevState>(work, L.off_state);
@@ -659,6 +662,7 @@ k_diag(Layout L, void* work, int J, int robust, int om, int nbc) {
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
     __syncwarp();
+    const long long t0 = clock64();  // the wait is bounded from the copy's issue
     if (lane == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes));
         asm volatile(
@@ -667,20 +671,27 @@ k_diag(Layout L, void* work, int J, int robust, int om, int nbc) {
             "l"(tile), "r"(bytes), "r"(mb)
             : "memory");
     }
-    long long spins = 0;
-    uint32_t done = 0;
-    while (true) {
+    // bounded wait: once wait_limit cycles have passed (checked before every
+    // poll) the error is recorded, and the block keeps waiting, at most
+    // kDrainCycles more, only so that the copy in flight lands before it
+    // returns
+    bool expired = false;
+    for (;;) {
+        const long long el = clock64() - t0;
+        if (!expired && el >= wait_limit) {
+            expired = true;
+            if (lane == 0) set_error(st, -6);  // HSEIN_ETIMEOUT
+        }
+        if (expired && el >= wait_limit + kDrainCycles) return;
+        uint32_t done = 0;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(mb)
             : "memory");
         if (done) break;
-        if (++spins > kWaitLimit) {  // the copy never completed: report and stop
-            if (lane == 0) set_error(st, -5);
-            return;
-        }
     }
+    if (expired) return;
     const int b = blockIdx.x;
     if (b < nbc) {
         constexpr int G = 32 / LPSC;
@@ -737,28 +748,26 @@ static int pow2_at_least(int v) {
 
 template <int RC, int RR>
 static void launch_t(const Layout& L, void* work, int J, int robust, int om, int nbc, int grid,
-                     size_t smem, cudaStream_t s) {
-    k_diag<kLpsC, RC, kLpsR, RR><<<grid, 32, smem, s>>>(L, work, J, robust, om, nbc);
+                     size_t smem, long long wl, cudaStream_t s) {
+    k_diag<kLpsC, RC, kLpsR, RR><<<grid, 32, smem, s>>>(L, work, J, robust, om, nbc, wl);
 }
 
 static size_t diag_smem(int br) {
     return ((size_t)br * br + (size_t)kMaxGroups * 7 * br) * sizeof(double);
 }
 
-void launch_diag(const Layout& L, void* work, const double* H, int ldh, int J, int robust,
-                 int omega_log2, cudaStream_t s) {
-    (void)H;
-    (void)ldh;
+void launch_diag(const Layout& L, void* work, int J, int robust, int omega_log2,
+                 long long wait_limit, cudaStream_t s) {
     const int nbc = (L.mc + (32 / kLpsC) - 1) / (32 / kLpsC);
     const int nbr = (L.mr + (32 / kLpsR) - 1) / (32 / kLpsR);
     const size_t smem = diag_smem(L.br);
     const int grid = nbc + nbr;
     // rows per lane, rounded up to a power of two: complex br/32, real br/16
     switch (pow2_at_least((L.br + kLpsR - 1) / kLpsR)) {
-        case 1: launch_t<1, 1>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
-        case 2: launch_t<1, 2>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
-        case 4: launch_t<2, 4>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
-        default: launch_t<4, 8>(L, work, J, robust, omega_log2, nbc, grid, smem, s); break;
+        case 1: launch_t<1, 1>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
+        case 2: launch_t<1, 2>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
+        case 4: launch_t<2, 4>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
+        default: launch_t<4, 8>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
     }
 }
 

@@ -51,3 +51,30 @@ def residuals(M, X, wr, wi, status=None):
             continue
         res.append(residual(M, lam, x))
     return np.array(res)
+
+
+def separation(eigs, lam):
+    """Distance from lam to the nearest other eigenvalue of the list eigs
+    (lam itself is one of them)."""
+    d = np.sort(np.abs(np.asarray(eigs) - lam))
+    return d[1] if len(d) > 1 else np.inf
+
+
+# Angle gate of the parity tests.  Two normwise backward-stable solves of
+# (H - lambda I) x = b whose backward errors are of order n eps ||H|| give
+# directions that differ, to first order, by about n eps ||H|| / gap, gap the
+# distance of lambda to the nearest other eigenvalue: each of the two lies
+# within that of the exact direction, so they lie within twice that of each
+# other (C_FO = 2).  Eigenvalues separated by >= 1e-3 ||H||_inf meet the
+# acceptance bound 1e-10 itself.
+C_FO = 2.0
+
+
+def first_order_bound(gap, hnorm, n):
+    return n * EPS * hnorm / gap if gap > 0 else np.inf
+
+
+def angle_bound(gap, hnorm, n):
+    if gap >= 1e-3 * hnorm:
+        return 1e-10
+    return max(1e-10, C_FO * first_order_bound(gap, hnorm, n))

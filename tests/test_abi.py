@@ -56,6 +56,8 @@ def test_status_strings(lib):
 def test_default_options(lib):
     o = hs.hsein_default_options()
     assert o.br == 64 and o.robust == 1 and o.omega_log2 == 1000 and o.precision == 0
+    assert o.wait_limit_cycles == 1 << 32
+    assert hs.hsein_status_string(-6) != "unknown status"
 
 
 @pytest.mark.parametrize("args", [(0, 1, 0), (4, -1, 0), (4, 0, -2), (4, 0, 0)])
@@ -66,7 +68,8 @@ def test_plan_rejects_bad_sizes(lib, args):
 
 
 def test_plan_rejects_bad_options(lib):
-    for field, value in [("br", 4), ("br", 129), ("omega_log2", 8), ("robust", 2), ("precision", 3)]:
+    for field, value in [("br", 4), ("br", 129), ("omega_log2", 8), ("robust", 2), ("precision", 3),
+                         ("wait_limit_cycles", -1), ("wait_limit_cycles", 1 << 61)]:
         o = hs.hsein_default_options()
         setattr(o, field, value)
         with pytest.raises(hs.HseinError) as e:

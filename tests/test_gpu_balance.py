@@ -21,7 +21,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2101_05063_gb300 as hs  # noqa: E402
-from tests.test_gpu_parity import separation, to_dev  # noqa: E402
+from tests.metrics import angle_bound, separation  # noqa: E402
+from tests.test_gpu_parity import to_dev  # noqa: E402
 
 
 def _graded(inst, u):
@@ -84,7 +85,7 @@ def test_balanced_split_solve_matches_the_oracle(n, mr, mc, seed):
         c0 = offs[l]
         xg = Xh[:, c0] + 1j * Xh[:, c0 + 1] if inst.wi[l] != 0 else Xh[:, c0]
         gap = separation(inst.eigs, vo[l][0])
-        bound = 1e-10 if gap >= 1e-3 * hn else max(1e-10, 1e3 * n * EPS * hn / gap)
+        bound = angle_bound(gap, hn, n)
         assert angle(xg, vo[l][1]) <= bound, (l, angle(xg, vo[l][1]), bound)
         checked += 1
     assert checked >= inst.m // 2

@@ -23,7 +23,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2101_05063_gb300 as hs  # noqa: E402
-from tests.test_gpu_parity import separation, to_dev  # noqa: E402
+from tests.metrics import angle_bound, separation  # noqa: E402
+from tests.test_gpu_parity import to_dev  # noqa: E402
 
 TILE = {0: lambda n: 64, 1: lambda n: 32 if n < 512 else 64,
         2: lambda n: 16 if n < 256 else (32 if n < 1024 else 64)}
@@ -81,7 +82,7 @@ def test_batch_matches_the_oracle(small_batch):
                 continue
             lam = vo[q][0]
             gap = separation(inst.eigs, lam)
-            bound = 1e-10 if gap >= 1e-3 * hn else max(1e-10, 1e3 * inst.n * EPS * hn / gap)
+            bound = angle_bound(gap, hn, inst.n)
             assert angle(Xh[:, offs[l]], vo[q][1]) <= bound
 
 

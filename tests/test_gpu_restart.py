@@ -23,7 +23,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2101_05063_gb300 as hs  # noqa: E402
-from tests.test_gpu_parity import separation, to_dev  # noqa: E402
+from tests.metrics import angle_bound, separation  # noqa: E402
+from tests.test_gpu_parity import to_dev  # noqa: E402
 
 
 def _start_without_left_component(H, lam, seed, cplx):
@@ -87,7 +88,7 @@ def test_restart_converges_from_an_orthogonal_start(cplx):
     xg = Xh[:, offs[l]] + 1j * Xh[:, offs[l] + 1] if cplx else Xh[:, offs[l]]
     hn = oracle.hnorm_inf(inst.H)
     gap = separation(inst.eigs, lam)
-    bound = 1e-10 if gap >= 1e-3 * hn else max(1e-10, 1e3 * n * EPS * hn / gap)
+    bound = angle_bound(gap, hn, n)
     assert angle(xg, vo) <= bound
 
 
@@ -174,6 +175,6 @@ def test_restart_full_size_matches_the_oracle():
             xg = Xh[:, c0] + 1j * Xh[:, c0 + 1] if inst.wi[l] != 0 else Xh[:, c0]
             lam = complex(inst.wr[l], inst.wi[l])
             gap = separation(inst.eigs, lam)
-            bound = 1e-10 if gap >= 1e-3 * hn else max(1e-10, 1e3 * n * EPS * hn / gap)
+            bound = angle_bound(gap, hn, n)
             assert angle(xg, vo) <= bound
     assert rc == (0 if (sh == 0).all() else 1)
