@@ -34,9 +34,13 @@ sys.path.insert(0, ROOT)
 METRIC = "eigvecs/s vs plain FP64 GPU at residual≤100nε; tensor-peak %; p50/p99 ms"
 UNIT = "eigvecs/s"
 EPS = 2.0 ** -53
-# FP64 peak: measured bf16 dense peak x the nominal FP64/BF16 ratio (1.25/2250);
-# a direct probe on this machine's GB300 measured 1.05 (DMMA), 1.01 (DFMA) and
-# 1.10 (cuBLAS DGEMM) TFLOP/s.
+# FP64 peak of the CUDA cores from unit counts and the clock: GB300's nominal
+# 1.25 TFLOP/s at 2070 MHz over 152 SMs is 2 FP64 FMAs (4 flops) per SM per
+# clock; the roofline takes that times the SM count times the median SM clock
+# sampled during the timed region.  Beside it: the rate the library's DFMA
+# probe reaches (hsein_fp64_rate) and the older estimate from the measured
+# BF16 peak x the nominal FP64/BF16 ratio 1.25/2250.
+FP64_FLOPS_PER_SM_CLK = 4.0
 NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
 
 
@@ -51,8 +55,12 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
-    ap.add_argument("--serve-requests", type=int, default=4000,
-                    help="requests in the serving stream (the full workload is 20000)")
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="requests in the serving stream at 200 requests/s (the workload)")
+    ap.add_argument("--capacity-requests", type=int, default=4000,
+                    help="requests per stream of the serving capacity sweep (0: skip)")
+    ap.add_argument("--no-c2", action="store_true", help="skip the n = 8192 precision workload")
+    ap.add_argument("--c2-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=256, help="shifts in the oracle sample")
     ap.add_argument("--no-reduction", action="store_true",
                     help="skip timing the Hessenberg reduction A -> (H, Q0)")
@@ -190,20 +198,112 @@ def update_flops(n, ncol, br):
 
 def diag_flops(inst, br):
     """Algorithmic flops of all diagonal-tile sweeps of one solve (k_diag, one
-    launch per tile).  Per shift and tile of height bt: the row updates of the
-    sweep, bt(bt-1)/2 rows of x -= a v - b t, v = c t + s v (7 flops real, 18
-    complex), a rotation with its division per step (10 / 20 flops), and the
-    Z'/W build (12 / 24 flops per row)."""
+    launch per tile column): 5 n b_r per solution column, the count of the
+    per-column work on the diagonal tiles (Table "flops-vector"; a complex
+    shift owns two columns).  Returns (total, launches)."""
     n = inst.n
     N = (n + br - 1) // br
-    b0 = n - (N - 1) * br
-    total = 0
-    for J in range(N):
-        bt = b0 if J == 0 else br
-        rows = bt * (bt - 1) // 2
-        total += inst.m_real * (7 * rows + 10 * (bt - 1) + 12 * bt)
-        total += inst.m_cplx * (18 * rows + 20 * (bt - 1) + 24 * bt)
-    return total, N
+    return 5.0 * n * br * inst.ncol, N
+
+
+def fp64_peak_tflops(sm_mhz, sms):
+    """FP64 CUDA-core peak from unit counts and the sampled SM clock."""
+    return FP64_FLOPS_PER_SM_CLK * sms * sm_mhz * 1e6 / 1e12
+
+
+def spawn_pool(workers, blas_threads):
+    """A pool of spawned processes (safe beside an initialized CUDA context)
+    whose BLAS uses blas_threads threads."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = str(blas_threads)
+    try:
+        ex = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+        ex.submit(int, 0).result()  # start the workers with these settings
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return ex
+
+
+def _gen_config2():
+    import hsein_inputs as hi
+    t0 = time.perf_counter()
+    inst = hi.config2()
+    return inst, time.perf_counter() - t0
+
+
+def _gen_serving_pool():
+    import hsein_inputs as hi
+    t0 = time.perf_counter()
+    pool = hi.serving_pool()
+    return pool, time.perf_counter() - t0
+
+
+def column_vectors(X, wr, wi):
+    """[(lambda, vector)] from the column layout (complex: [re, im])."""
+    import numpy as np
+    out, c = [], 0
+    for l in range(len(wr)):
+        if wi[l] != 0:
+            out.append((complex(wr[l], wi[l]), X[:, c] + 1j * X[:, c + 1]))
+            c += 2
+        else:
+            out.append((float(wr[l]), X[:, c]))
+            c += 1
+    return out
+
+
+def chordal_angle(x, y):
+    import numpy as np
+    x = np.asarray(x, dtype=np.complex128)
+    y = np.asarray(y, dtype=np.complex128)
+    nx, ny = np.linalg.norm(x), np.linalg.norm(y)
+    if nx == 0 or ny == 0:
+        return float("inf")
+    x, y = x / nx, y / ny
+    d = np.vdot(y, x)
+    return float(np.linalg.norm(x - y * (d / abs(d) if abs(d) > 0 else 1.0)))
+
+
+def accuracy_vs_oracle(inst, idx, Xg, sg, Xo, so, hnorm):
+    """Angles between the GPU's and the oracle's eigenvectors for the sampled
+    shifts idx (Xo, so: the oracle's results for them), the worst ratio to the
+    first-order bound n eps ||H|| / gap (gap = distance to the nearest other
+    eigenvalue) and whether the statuses agree."""
+    import numpy as np
+    import hsein_inputs as hi
+    offs = hi.column_offsets(inst.wi)
+    vo = column_vectors(Xo, inst.wr[idx], inst.wi[idx])
+    worst, worst_ratio, worst_sep, n_sep, cnt = 0.0, 0.0, 0.0, 0, 0
+    eigs = np.asarray(inst.eigs)
+    for j, l in enumerate(idx):
+        if sg[l] != 0 or so[j] != 0:
+            continue
+        c0, c1 = offs[l], offs[l + 1]
+        xg = Xg[:, c0] + 1j * Xg[:, c0 + 1] if c1 - c0 == 2 else Xg[:, c0]
+        lam = vo[j][0]
+        a = chordal_angle(xg, vo[j][1])
+        d = np.sort(np.abs(eigs - lam))
+        gap = d[1] if len(d) > 1 else np.inf
+        worst = max(worst, a)
+        worst_ratio = max(worst_ratio, a / (inst.n * EPS * hnorm / gap))
+        if gap >= 1e-3 * hnorm:
+            n_sep += 1
+            worst_sep = max(worst_sep, a)
+        cnt += 1
+    return {"angle_max_vs_oracle": worst,
+            "angle_over_first_order_bound_max": worst_ratio,
+            "angle_max_separated": worst_sep if n_sep else None, "separated_columns": n_sep,
+            "columns_compared": cnt,
+            "status_equal": bool(np.array_equal(np.asarray(sg)[idx], so)),
+            "gate": "angle <= 1e-10 (gap >= 1e-3 ||H||_inf), else <= 2 n eps ||H|| / gap"}
 
 
 def source_hash(relpath):
@@ -250,7 +350,7 @@ def cpu_baseline(inst, sample_shifts):
     cores = os.cpu_count()
     desc = ("%d of %d shifts (%d columns) of the same instance: Henry solve + normalization + "
             "backtransform + z = Q0 x, OpenMP over shifts, %.2f s wall" % (len(idx), inst.m, cols, dt))
-    return cols / dt, cores, desc
+    return cols / dt, cores, desc, (idx, X, st)
 
 
 def run_reference(args):
@@ -299,7 +399,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def measure_batch(args, torch, hs, hi):
+def measure_batch(args, torch, hs, hi, fp64_peak):
     """The batching workload (256 independent instances, n log-uniform in
     [64, 2048], all real eigenvalues as shifts, FP64 throughout) in one
     captured CUDA graph per batch, configuration chosen by the autotuner."""
@@ -324,19 +424,39 @@ def measure_batch(args, torch, hs, hi):
     conv = sum(int((st.cpu().numpy() == 0).sum()) for st in b.status)  # real shifts: 1 column each
     total = sum(i.m for i in insts)
     ms = float(np.mean(per))
+    # algorithmic flops of the batch at the chosen tile heights: every
+    # instance's shared-H products and diagonal-tile sweeps
+    pol = cfg.get("br_policy", 0)
+
+    def br_of(n):
+        if pol == 1:
+            return 32 if n < 512 else 64
+        if pol == 2:
+            return 16 if n < 256 else (32 if n < 1024 else 64)
+        return 64
+    flops = 0.0
+    for i in insts:
+        br = br_of(i.n)
+        flops += update_flops(i.n, i.ncol, br)[0] + diag_flops(i, br)[0]
+    achieved = flops / (ms * 1e-3) / 1e12
     return {"workload": "256 independent instances, n = round(exp(U[ln 64, ln 2048])), 25%% with "
                         "complex pairs, all real eigenvalues as shifts (%d), FP64" % total,
             "value": conv / (ms * 1e-3), "unit": UNIT, "ms_per_batch": ms,
             "latency": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
                         "unit": "ms", "of": "%d batches" % args.batch_steps},
             "converged_columns": conv, "columns": total, "autotuned": cfg,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                         "algorithmic_flops": flops,
+                         "what": "shared-H products (2 p0 b_r 2 ncol per tile column) + "
+                                 "diagonal-tile sweeps (5 n b_r per column), all instances"},
             "autotune_ms_best": ms_tune, "host_launches_per_batch": 1,
             "generation_s": t_gen, "sizes": {"min": min(i.n for i in insts),
                                              "max": max(i.n for i in insts),
                                              "sum": sum(i.n for i in insts)}}
 
 
-def replay_stream(srv, pool_dev, reqs, torch, keep=True):
+def replay_stream(srv, pool_dev, reqs, torch, keep=True, precision=1):
     """Replay a request stream in real time on a hs.Server: each request is
     submitted at its arrival time (seconds after the start) and progress()
     is driven in between.  pool_dev[n][i] = (H, Hb, e): the matrix, the
@@ -361,8 +481,8 @@ def replay_stream(srv, pool_dev, reqs, torch, keep=True):
             r = reqs[i]
             H, Hb, e = pool_dev[r["n"]][r["index"]]
             # graded requests run on the balanced form of their matrix
-            tk = srv.submit(Hb if r["graded"] else H, shifts[i][0], shifts[i][1], precision=1,
-                            exps=e if r["graded"] else None)
+            tk = srv.submit(Hb if r["graded"] else H, shifts[i][0], shifts[i][1],
+                            precision=precision, exps=e if r["graded"] else None)
             of[tk] = i
             i += 1
         done = srv.progress(wait=(i == len(reqs)))
@@ -377,20 +497,20 @@ def replay_stream(srv, pool_dev, reqs, torch, keep=True):
     return [(r["t"], t_done[j]) for j, r in enumerate(reqs)], results
 
 
-def measure_serving(args, torch, hs, hi):
+def measure_serving(args, torch, hs, hi, pool, t_gen):
     """The serving workload: a Poisson stream (200 requests/s) of solves on a
-    pre-generated pool, replayed in real time through hs.Server."""
+    pre-generated pool, replayed in real time through hs.Server; then the
+    capacity sweep: shorter streams at 2, 4 and 8 times the rate, and the
+    8-times stream again with FP64 products (precision 0) for every request,
+    so that the saturated throughput of the split-precision service stands
+    beside the plain FP64 service's."""
     import numpy as np
-    t0 = time.perf_counter()
-    pool = hi.serving_pool()
-    t_gen = time.perf_counter() - t0
     f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device="cuda")
     pool_dev = {n: [(f(i.H),) + tuple(hs.balance(f(i.Hg))) for i in lst]
                 for n, lst in pool.items()}
     torch.cuda.synchronize()
-    reqs = hi.serving_requests(pool, args.serve_requests)
     srv = hs.Server(64 << 30, max_jobs=8, max_merge_shifts=4096)
-    # warm-up: one request per size class, outside the stream
+    # warm-up: one request per size class and kind, outside the stream
     warm = [dict(r, t=0.0) for r in hi.serving_requests(pool, 64, seed=41)]
     seen, wl = set(), []
     for r in warm:
@@ -398,27 +518,60 @@ def measure_serving(args, torch, hs, hi):
             seen.add((r["n"], r["graded"]))
             wl.append(r)
     replay_stream(srv, pool_dev, wl, torch, keep=False)
-    s0 = srv.stats()
-    times, status = replay_stream(srv, pool_dev, reqs, torch, keep=False)
-    s1 = srv.stats()
-    lat = np.array([c - a for a, c in times]) * 1e3
-    conv = sum(int(sum(2 if w != 0 else 1 for w, st in zip(r["wi"], status[j]) if st == 0))
-               for j, r in enumerate(reqs))
-    cols = sum(len(r["wr"]) + int((r["wi"] != 0).sum()) for r in reqs)
-    span = max(c for a, c in times)
-    return {"workload": "Poisson stream, 200 requests/s, %d requests; n uniform over %s, k "
-                        "uniform in [1, n/4]; 30%% graded D H D^-1 (u ~ U[-150, 150]) solved "
-                        "on their power-of-two balanced form; 30%% with complex pairs; "
-                        "split-precision products; rho e starting vectors"
-                        % (len(reqs), list(hi.SERVE_SIZES)),
-            "value": conv / span, "unit": UNIT, "span_s": span,
-            "latency": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                        "unit": "ms", "of": "%d requests, arrival to completion" % len(reqs)},
-            "converged_columns": conv, "columns": cols,
-            "requests_admitted": s1["requests_admitted"] - s0["requests_admitted"],
-            "solves_admitted": s1["solves_admitted"] - s0["solves_admitted"],
-            "server": {"arena_gb": 64, "max_jobs": 8, "max_merge_shifts": 4096},
-            "pool": {str(n): len(v) for n, v in pool.items()}, "generation_s": t_gen}
+    replay_stream(srv, pool_dev, wl, torch, keep=False, precision=0)
+
+    def run(count, rate, precision, seed=4):
+        reqs = hi.serving_requests(pool, count, seed=seed, rate=rate)
+        s0 = srv.stats()
+        times, status = replay_stream(srv, pool_dev, reqs, torch, keep=False, precision=precision)
+        s1 = srv.stats()
+        lat = np.array([c - a for a, c in times]) * 1e3
+        conv = sum(int(sum(2 if w != 0 else 1 for w, st in zip(r["wi"], status[j]) if st == 0))
+                   for j, r in enumerate(reqs))
+        cols = sum(len(r["wr"]) + int((r["wi"] != 0).sum()) for r in reqs)
+        span = max(c for a, c in times)
+        return {"rate_per_s": rate, "requests": count,
+                "precision": "split" if precision == 1 else "fp64",
+                "value": conv / span, "unit": UNIT, "span_s": span,
+                "arrival_span_s": reqs[-1]["t"],
+                "latency": {"p50": float(np.percentile(lat, 50)),
+                            "p99": float(np.percentile(lat, 99)), "unit": "ms"},
+                "converged_columns": conv, "columns": cols,
+                "requests_admitted": s1["requests_admitted"] - s0["requests_admitted"],
+                "solves_admitted": s1["solves_admitted"] - s0["solves_admitted"]}
+
+    main = run(args.serve_requests, 200.0, 1)
+    out = {"workload": "Poisson stream, 200 requests/s, %d requests; n uniform over %s, k "
+                       "uniform in [1, n/4]; 30%% graded D H D^-1 (u ~ U[-150, 150]) solved "
+                       "on their power-of-two balanced form; 30%% with complex pairs; "
+                       "split-precision products; rho e starting vectors"
+                       % (args.serve_requests, list(hi.SERVE_SIZES)),
+           "value": main["value"], "unit": UNIT, "span_s": main["span_s"],
+           "latency": dict(main["latency"], of="%d requests, arrival to completion"
+                           % args.serve_requests),
+           "converged_columns": main["converged_columns"], "columns": main["columns"],
+           "requests_admitted": main["requests_admitted"],
+           "solves_admitted": main["solves_admitted"],
+           "server": {"arena_gb": 64, "max_jobs": 8, "max_merge_shifts": 4096},
+           "pool": {str(n): len(v) for n, v in pool.items()}, "generation_s": t_gen,
+           "value_is": "converged columns / (last completion - first arrival): the offered "
+                       "load while the service keeps up (see capacity)"}
+    if args.capacity_requests > 0:
+        cap = [run(args.capacity_requests, 200.0 * k, 1, seed=50 + k) for k in (2, 4, 8)]
+        cap.append(run(args.capacity_requests, 1600.0, 0, seed=58))
+        sat = [c for c in cap if c["span_s"] > 1.2 * c["arrival_span_s"]]
+        out["capacity"] = {
+            "streams": cap,
+            "saturated_split_value": max((c["value"] for c in cap if c["precision"] == "split"),
+                                         default=None),
+            "saturated_fp64_value": cap[-1]["value"],
+            "split_over_fp64": cap[2]["value"] / cap[-1]["value"] if cap[-1]["value"] else None,
+            "saturated_streams": [(c["rate_per_s"], c["precision"]) for c in sat],
+            "how": "%d-request streams at 2x, 4x, 8x the rate (split products) and at 8x with "
+                   "FP64 products; a stream whose completion span exceeds its arrival span is "
+                   "saturated, and its eigvecs/s is the service's capacity"
+                   % args.capacity_requests}
+    return out
 
 
 def measure_reduction(inst, torch, hs, fp64_peak):
@@ -458,6 +611,135 @@ def measure_reduction(inst, torch, hs, fp64_peak):
                        "nonzeros_below_subdiagonal": below}}
 
 
+def residual_max_device(torch, dH, X, wr, wi, status, n):
+    """Largest normwise residual ||H x - lambda x||_1 / (||H||_1 ||x||_1) over
+    the converged columns, in units of n eps (FP64 on the device)."""
+    import numpy as np
+    import hsein_inputs as hi
+    HX = dH @ X
+    hn1 = float(dH.abs().sum(dim=0).max())
+    st = status.cpu().numpy()
+    offs = hi.column_offsets(wi)
+    ok = st == 0
+    dev = X.device
+    worst = 0.0
+    re = np.nonzero(ok & (np.asarray(wi) == 0))[0]
+    if len(re):
+        c = torch.as_tensor(offs[re], device=dev)
+        lam = torch.as_tensor(np.asarray(wr)[re], dtype=torch.float64, device=dev)
+        num = (HX[:, c] - X[:, c] * lam).abs().sum(dim=0)
+        den = X[:, c].abs().sum(dim=0)
+        worst = max(worst, float((num / (hn1 * den)).max()))
+    cx = np.nonzero(ok & (np.asarray(wi) != 0))[0]
+    if len(cx):
+        c = torch.as_tensor(offs[cx], device=dev)
+        lr = torch.as_tensor(np.asarray(wr)[cx], dtype=torch.float64, device=dev)
+        li = torch.as_tensor(np.asarray(wi)[cx], dtype=torch.float64, device=dev)
+        xr, xi, hr, hi_ = X[:, c], X[:, c + 1], HX[:, c], HX[:, c + 1]
+        rr = hr - xr * lr + xi * li
+        ri = hi_ - xi * lr - xr * li
+        num = torch.sqrt(rr * rr + ri * ri).sum(dim=0)
+        den = torch.sqrt(xr * xr + xi * xi).sum(dim=0)
+        worst = max(worst, float((num / (hn1 * den)).max()))
+    return worst / (n * EPS)
+
+
+def measure_instance(torch, hs, inst, precision, steps, warmup, br=64, keep=False):
+    """Time `steps` steps (hsein_solve + hsein_backtransform) of one instance
+    in one precision mode, inputs resident in HBM; per-step latency, phases,
+    residuals and converged columns."""
+    import numpy as np
+    import hsein_inputs as hi
+    f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device="cuda")
+    dH, dwr, dwi, dB, dQ = f(inst.H), f(inst.wr), f(inst.wi), f(inst.B), f(inst.Q0)
+    n, ncol = inst.n, inst.ncol
+    X = torch.empty((ncol, n), dtype=torch.float64, device="cuda").t()
+    Z = torch.empty((ncol, n), dtype=torch.float64, device="cuda").t()
+    status = torch.empty(inst.m, dtype=torch.int32, device="cuda")
+    solver = hs.Solver(n, inst.m_real, inst.m_cplx, br=br, precision=precision)
+
+    def step():
+        solver.solve(dH, dwr, dwi, dB, X=X, status=status, check=False)
+        solver.backtransform(dQ, X, Z=Z)
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    if solver.device_status() < 0:
+        raise RuntimeError("device status %d" % solver.device_status())
+    hs.hsein_plan_set_profiling(solver.plan, True)
+    hs.hsein_plan_profile(solver.plan, reset=True)
+    stream = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for i in range(steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    prof = hs.hsein_plan_profile(solver.plan, reset=True)
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    ms = float(sum(per)) / steps
+    sh = status.cpu().numpy()
+    offs = hi.column_offsets(inst.wi)
+    conv = int(sum(offs[l + 1] - offs[l] for l in range(inst.m) if sh[l] == 0))
+    out = {"value": conv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "latency": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                       "unit": "ms", "of": "%d steps" % steps},
+           "residual_max_over_n_eps": residual_max_device(torch, dH, X, inst.wr, inst.wi,
+                                                          status, n),
+           "not_converged": int((sh != 0).sum()), "converged_columns": conv,
+           "phases": {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
+                      for k, v in prof.items()}}
+    host = (X.cpu().numpy(), sh) if keep else None
+    del solver, dH, dQ, dB, X, Z
+    torch.cuda.empty_cache()
+    return out, host
+
+
+def measure_config2(args, torch, hs, inst, t_gen, fp64_peak, bf16_peak):
+    """The precision workload (n = 8192, 2048 real shifts): split-precision
+    products against FP64 products on the same instance, with the angles of a
+    seeded sample of columns against the oracle."""
+    import numpy as np
+    import hsein_inputs as hi
+    import oracle
+    sp, (Xs, ss) = measure_instance(torch, hs, inst, 1, args.c2_steps, args.warmup, keep=True)
+    fp, (Xf, sf) = measure_instance(torch, hs, inst, 0, 2, 3, keep=True)
+    idx = np.sort(np.argsort(hi.uniform(4242, 7, inst.m), kind="stable")[:64])
+    Xo, so = oracle.hsein(inst.H, inst.wr[idx], inst.wi[idx], inst.B[:, idx])
+    hn = oracle.hnorm_inf(inst.H)
+    sp["accuracy"] = accuracy_vs_oracle(inst, idx, Xs, ss, Xo, so, hn)
+    fp["accuracy"] = accuracy_vs_oracle(inst, idx, Xf, sf, Xo, so, hn)
+    # split against FP64 products, every converged column
+    worst = 0.0
+    for l in np.nonzero((ss == 0) & (sf == 0))[0]:
+        worst = max(worst, chordal_angle(Xs[:, l], Xf[:, l]))
+    uf, ul = update_flops(inst.n, inst.ncol, 64)
+    q0f = 2.0 * inst.n * inst.n * inst.ncol
+    ph = sp["phases"]
+    df, dl = diag_flops(inst, 64)
+    t_diag = ph["diag_sweep"]["ms_per_step"] / max(1e-9, ph["diag_sweep"]["launches_per_step"])
+    sp["roofline_k_diag"] = {"bound": "alu", "achieved": df / dl / (t_diag * 1e-3) / 1e12,
+                             "peak": fp64_peak, "unit": "TFLOP/s"}
+    sp["roofline_k_diag"]["frac"] = sp["roofline_k_diag"]["achieved"] / fp64_peak
+    sp["tensor"] = {
+        "peak": bf16_peak, "unit": "TFLOP/s",
+        "shared_h_update_frac": 28.0 * uf / (ph["shared_h_update"]["ms_per_step"] * 1e-3) / 1e12
+        / bf16_peak,
+        "q0_backtransform_frac": 28.0 * q0f / (ph["q0_backtransform"]["ms_per_step"] * 1e-3)
+        / 1e12 / bf16_peak}
+    t_upd = fp["phases"]["shared_h_update"]["ms_per_step"]
+    fp["roofline_k_update"] = {"bound": "alu", "achieved": uf / (t_upd * 1e-3) / 1e12,
+                               "peak": fp64_peak, "unit": "TFLOP/s"}
+    fp["roofline_k_update"]["frac"] = fp["roofline_k_update"]["achieved"] / fp64_peak
+    return {"workload": "n = 8192, 2048 real shifts, eigenvalues U[-n, n] with minimum gap "
+                        "1e-2, tile height 64; split-precision products (BF16 digit slices on "
+                        "the tensor cores) against FP64 products",
+            "split": sp, "fp64": fp,
+            "split_over_fp64": sp["value"] / fp["value"] if fp["value"] else None,
+            "angle_max_split_vs_fp64": worst, "generation_s": t_gen}
+
+
 def workload_config(inst, br):
     return {
         "workload": "mixed real/complex shifts: n=4096, 512 real + 256 complex shifts "
@@ -480,6 +762,15 @@ def main():
     import paper_2101_05063_gb300 as hs
 
     rank, world, local = dist_setup()
+    # the larger workloads' inputs are generated in spawned processes while
+    # the GPU measures the headline workload
+    bg, futs = None, {}
+    if rank == 0 and world == 1 and (not args.no_c2 or not args.no_serve):
+        bg = spawn_pool(2, max(1, (os.cpu_count() or 2) // 3))
+        if not args.no_c2:
+            futs["c2"] = bg.submit(_gen_config2)
+        if not args.no_serve:
+            futs["serve"] = bg.submit(_gen_serving_pool)
     dev = torch.device("cuda", local)
     inst = hi.config1(seed=rank_seed(rank), keep_a=True)
     n, ncol, m = inst.n, inst.ncol, inst.m
@@ -583,6 +874,7 @@ def main():
 
     # ---------------- the plain FP64 path (the metric's comparison) --------
     solver, step, ms, prof, worst, sh, clocks, lat = measure(0, True)
+    X_plain = X.cpu().numpy()
     conv_cols = converged_columns(sh)
     all_cols = sum_over_ranks(conv_cols, world)
     value = all_cols * args.steps / (ms * 1e-3)
@@ -591,6 +883,7 @@ def main():
 
     # ---------------- the split-precision path: the headline ---------------
     solver_sp, step_sp, ms_sp, prof_sp, worst_sp, sh_sp, clocks_sp, lat_sp = measure(1, True)
+    X_sp = X.cpu().numpy()
     conv_sp = converged_columns(sh_sp)
     all_sp = sum_over_ranks(conv_sp, world)
     value_sp = all_sp * args.steps / (ms_sp * 1e-3)
@@ -641,14 +934,25 @@ def main():
     if rank != 0:
         return
     pk, pk_kind = peaks()
-    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16  # TFLOP/s
-    peak_source = ("FP64: %s bf16 %.1f TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
-                   % (pk_kind, pk["bf16_tflops"]))
-    uf, ulaunch = update_flops(n, ncol, args.br)
-    q0f = 2.0 * n * n * ncol
-    per_phase = lambda pr: {k: {"ms_per_step": v[0] / args.steps,
-                                "launches_per_step": v[1] / args.steps} for k, v in pr.items()}
-
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (clocks_sp or {}).get("sm_mhz") or 2070.0
+    fp64_peak = fp64_peak_tflops(sm_mhz, sms)
+    probe_sampler = ClockSampler(torch.cuda.current_device())
+    probe_sampler.start()
+    probe, probe_all = hs.fp64_rate(iters=50000, repeats=5)
+    probe_clocks = probe_sampler.stop()
+    fp64_peak_info = {
+        "peak_tflops": fp64_peak,
+        "how": "4 flops (2 FP64 FMA) per SM per clock x %d SMs x %.0f MHz (median SM clock "
+               "sampled during the timed region)" % (sms, sm_mhz),
+        "probe_tflops": probe, "probe_clocks": probe_clocks,
+        "probe_how": "hsein_fp64_rate: eight independent DFMA chains per thread, %d threads, "
+                     "median of 5 launches (CUDA events)" % (sms * 1024),
+        "bf16_derived_tflops": pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16,
+        "bf16_derived_how": "%s bf16 %.1f TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
+                            % (pk_kind, pk["bf16_tflops"])}
+    peak_source = "FP64 CUDA cores: unit counts x sampled clock (%.3f TFLOP/s); probe %.3f" % (
+        fp64_peak, probe)
     # plain FP64 path: its dominant kernel is the shared-H product k_update
     # (or z = Q0 x when that takes longer)
     if max(prof, key=lambda k: prof[k][0]) == "q0_backtransform":
@@ -678,7 +982,8 @@ def main():
         "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved,
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "traffic": profiled_traffic(kfile, summary), "peak_source": peak_source,
-                     "algorithmic_flops_per_launch": flops_launch},
+                     "algorithmic_flops_per_launch": flops_launch,
+                     "frac_of_probe": achieved / probe},
     }
 
     # split path: the digit products run on the BF16 tensor cores; 28 digit
@@ -697,6 +1002,7 @@ def main():
     df, dlaunch = diag_flops(inst, args.br)
     t_diag = prof_sp["diag_sweep"][0] / max(1, prof_sp["diag_sweep"][1])
     achieved_d = df / dlaunch / (t_diag * 1e-3) / 1e12
+    bf_d = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
     line = {
         "metric": METRIC, "value": value_sp, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_sp / args.steps, "latency": lat_sp,
@@ -710,7 +1016,11 @@ def main():
                      "traffic": profiled_traffic("paper_2101_05063_gb300/csrc/k_diag.cu",
                                                  "k_diag_config1.txt"),
                      "peak_source": peak_source,
-                     "algorithmic_flops_per_launch": df / dlaunch},
+                     "algorithmic_flops_per_launch": df / dlaunch,
+                     "flop_count": "5 n b_r per column per solve (per launch: 5 b_r^2 ncol)",
+                     "frac_of_probe": achieved_d / probe,
+                     "frac_of_bf16_derived": achieved_d / bf_d},
+        "fp64_peak": fp64_peak_info,
         "tensor": tensor,
         "phases": per_phase(prof_sp),
         "residual_max_over_n_eps": worst_sp,
@@ -729,14 +1039,33 @@ def main():
     }
     if not args.no_reduction and world == 1:
         line["reduction"] = measure_reduction(inst, torch, hs, fp64_peak)
+    if world == 1:
+        c0 = hi.config0()
+        sp0, _ = measure_instance(torch, hs, c0, 1, args.steps, args.warmup)
+        fp0, _ = measure_instance(torch, hs, c0, 0, args.steps, args.warmup)
+        line["config0"] = {"workload": "n = 512, 64 real shifts (the prescribed eigenvalues), "
+                                       "tile height 64", "split": sp0, "fp64": fp0}
+    if "c2" in futs:
+        c2, t_c2 = futs["c2"].result()
+        line["precision_c2"] = measure_config2(args, torch, hs, c2, t_c2, fp64_peak,
+                                               pk["bf16_tflops"])
+        del c2
     if not args.no_batch and world == 1:
-        line["batching"] = measure_batch(args, torch, hs, hi)
-    if not args.no_serve and world == 1:
-        line["serving"] = measure_serving(args, torch, hs, hi)
+        line["batching"] = measure_batch(args, torch, hs, hi, fp64_peak)
+    if "serve" in futs:
+        pool, t_pool = futs["serve"].result()
+        line["serving"] = measure_serving(args, torch, hs, hi, pool, t_pool)
+        del pool
+    if bg is not None:
+        bg.shutdown()
     if not args.no_cpu_baseline and world == 1:
-        v, cores, desc = cpu_baseline(inst, args.cpu_sample)
+        v, cores, desc, (idx, Xo, so) = cpu_baseline(inst, args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc}
+        import oracle
+        hn = oracle.hnorm_inf(inst.H)
+        line["accuracy"] = accuracy_vs_oracle(inst, idx, X_sp, sh_sp, Xo, so, hn)
+        line["plain_fp64"]["accuracy"] = accuracy_vs_oracle(inst, idx, X_plain, sh, Xo, so, hn)
     print(json.dumps(line), flush=True)
 
 

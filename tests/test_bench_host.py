@@ -2,7 +2,7 @@
 
 The algorithmic flop counts are checked against brute-force loops over the
 tiled schedule written out step by step (every product column of every tile
-update; every row update, rotation and Z'/W row of every sweep), and the
+update; every row of every diagonal tile and column), and the
 traffic lookup against a committed-summary stand-in: the figure is reported
 only while the kernel source matches the hash the capture was taken on.
 """
@@ -19,6 +19,7 @@ import bench  # noqa: E402
 class _Inst:
     def __init__(self, n, m_real, m_cplx):
         self.n, self.m_real, self.m_cplx = n, m_real, m_cplx
+        self.ncol = m_real + 2 * m_cplx
 
 
 def _tiles(n, br):
@@ -46,19 +47,18 @@ def test_update_flops_brute_force(n, br, ncol):
     assert total == brute
 
 
-@pytest.mark.parametrize("n,br,mr,mc", [(4096, 64, 512, 256), (200, 64, 3, 2), (64, 64, 1, 0)])
+@pytest.mark.parametrize("n,br,mr,mc", [(4096, 64, 512, 256), (200, 64, 3, 2), (64, 64, 1, 0),
+                                         (130, 32, 4, 3)])
 def test_diag_flops_brute_force(n, br, mr, mc):
+    # the per-column count of the diagonal-tile work (Table "flops-vector"):
+    # 5 b_r flops per row of every diagonal tile and solution column (a
+    # complex shift owns two columns)
     total, launches = bench.diag_flops(_Inst(n, mr, mc), br)
     brute = 0
     for (_p0, bt) in _tiles(n, br):
-        for cplx, count in ((False, mr), (True, mc)):
-            per = 0
-            for k in range(bt - 1, 0, -1):  # rotation k updates rows 0 .. k-1
-                per += 20 if cplx else 10
-                for _i in range(k):
-                    per += 18 if cplx else 7
-            per += bt * (24 if cplx else 12)  # the Z'/W build
-            brute += count * per
+        for _col in range(mr + 2 * mc):
+            for _row in range(bt):
+                brute += 5 * br
     assert launches == len(_tiles(n, br))
     assert total == brute
 
