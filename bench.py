@@ -44,6 +44,15 @@ FP64_FLOPS_PER_SM_CLK = 4.0
 NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line is the only stdout output)."""
+    sys.stderr.write("[bench %7.1f s] %s\n" % (time.perf_counter() - _T0, msg))
+    sys.stderr.flush()
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -772,7 +781,9 @@ def main():
         if not args.no_serve:
             futs["serve"] = bg.submit(_gen_serving_pool)
     dev = torch.device("cuda", local)
+    log("generating the n = 4096 workload")
     inst = hi.config1(seed=rank_seed(rank), keep_a=True)
+    log("generated")
     n, ncol, m = inst.n, inst.ncol, inst.m
     f = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64, device=dev)
     dH, dwr, dwi, dB, dQ = f(inst.H), f(inst.wr), f(inst.wi), f(inst.B), f(inst.Q0)
@@ -873,6 +884,7 @@ def main():
         return int(sum(offs[l + 1] - offs[l] for l in range(m) if sh_[l] == 0))
 
     # ---------------- the plain FP64 path (the metric's comparison) --------
+    log("plain FP64 path")
     solver, step, ms, prof, worst, sh, clocks, lat = measure(0, True)
     X_plain = X.cpu().numpy()
     conv_cols = converged_columns(sh)
@@ -882,6 +894,7 @@ def main():
     del solver
 
     # ---------------- the split-precision path: the headline ---------------
+    log("split-precision path")
     solver_sp, step_sp, ms_sp, prof_sp, worst_sp, sh_sp, clocks_sp, lat_sp = measure(1, True)
     X_sp = X.cpu().numpy()
     conv_sp = converged_columns(sh_sp)
@@ -889,6 +902,7 @@ def main():
     value_sp = all_sp * args.steps / (ms_sp * 1e-3)
     e2e_value_sp = all_sp * args.steps / (time_e2e(solver_sp) * 1e-3)
 
+    log("restart")
     # restart (Alg. "hsrq3in") of the shifts that did not converge, timed once
     # after a fresh solve: the cost of making every column converge
     step_sp()
@@ -906,6 +920,7 @@ def main():
                "unit": UNIT}
     del solver_sp
 
+    log("compact storage")
     # the headline path with the rotations stored compactly (Sec. 4.4)
     solver_c, _, ms_c, prof_c, worst_c, sh_c, _, lat_c = measure(1, False, givens=1, steps=5)
     compact = {"value": sum_over_ranks(converged_columns(sh_c), world) * 5 / (ms_c * 1e-3),
@@ -921,6 +936,7 @@ def main():
     # the comparison baseline: Henry's solve per shift, unblocked (the RQIN of
     # the paper's experiments), FP64, same workload, same backtransform
     bsteps = 3
+    log("per-shift baseline")
     _, _, ms_b, prof_b, worst_b, sh_b, _, lat_b = measure(0, False, method=1, steps=bsteps)
     conv_b = converged_columns(sh_b)
     baseline = {"method": "Henry's RQ solve per shift, unblocked (one thread block per shift "
@@ -937,6 +953,7 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = (clocks_sp or {}).get("sm_mhz") or 2070.0
     fp64_peak = fp64_peak_tflops(sm_mhz, sms)
+    log("FP64 probe")
     probe_sampler = ClockSampler(torch.cuda.current_device())
     probe_sampler.start()
     probe, probe_all = hs.fp64_rate(iters=50000, repeats=5)
@@ -953,6 +970,10 @@ def main():
                             % (pk_kind, pk["bf16_tflops"])}
     peak_source = "FP64 CUDA cores: unit counts x sampled clock (%.3f TFLOP/s); probe %.3f" % (
         fp64_peak, probe)
+    uf, ulaunch = update_flops(n, ncol, args.br)
+    q0f = 2.0 * n * n * ncol
+    per_phase = lambda pr: {k: {"ms_per_step": v[0] / args.steps,
+                                "launches_per_step": v[1] / args.steps} for k, v in pr.items()}
     # plain FP64 path: its dominant kernel is the shared-H product k_update
     # (or z = Q0 x when that takes longer)
     if max(prof, key=lambda k: prof[k][0]) == "q0_backtransform":
@@ -1038,27 +1059,35 @@ def main():
         "compact_givens": compact,
     }
     if not args.no_reduction and world == 1:
+        log("reduction")
         line["reduction"] = measure_reduction(inst, torch, hs, fp64_peak)
     if world == 1:
+        log("n = 512 workload")
         c0 = hi.config0()
         sp0, _ = measure_instance(torch, hs, c0, 1, args.steps, args.warmup)
         fp0, _ = measure_instance(torch, hs, c0, 0, args.steps, args.warmup)
         line["config0"] = {"workload": "n = 512, 64 real shifts (the prescribed eigenvalues), "
                                        "tile height 64", "split": sp0, "fp64": fp0}
     if "c2" in futs:
+        log("waiting for the n = 8192 workload")
         c2, t_c2 = futs["c2"].result()
+        log("n = 8192 workload")
         line["precision_c2"] = measure_config2(args, torch, hs, c2, t_c2, fp64_peak,
                                                pk["bf16_tflops"])
         del c2
     if not args.no_batch and world == 1:
+        log("batching")
         line["batching"] = measure_batch(args, torch, hs, hi, fp64_peak)
     if "serve" in futs:
+        log("waiting for the serving pool")
         pool, t_pool = futs["serve"].result()
+        log("serving")
         line["serving"] = measure_serving(args, torch, hs, hi, pool, t_pool)
         del pool
     if bg is not None:
         bg.shutdown()
     if not args.no_cpu_baseline and world == 1:
+        log("cpu baseline")
         v, cores, desc, (idx, Xo, so) = cpu_baseline(inst, args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc}
@@ -1066,6 +1095,7 @@ def main():
         hn = oracle.hnorm_inf(inst.H)
         line["accuracy"] = accuracy_vs_oracle(inst, idx, X_sp, sh_sp, Xo, so, hn)
         line["plain_fp64"]["accuracy"] = accuracy_vs_oracle(inst, idx, X_plain, sh, Xo, so, hn)
+    log("done")
     print(json.dumps(line), flush=True)
 
 

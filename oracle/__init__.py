@@ -60,6 +60,17 @@ def _bind(lib):
     lib.oracle_hsein.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp,
                                  ctypes.c_int, dp, ctypes.c_int, ip, ip, ctypes.c_double,
                                  ctypes.c_int, ctypes.c_int]
+    lib.oracle_lu_real.restype = ctypes.c_int
+    lib.oracle_lu_real.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, dp,
+                                   ctypes.c_double, ctypes.c_int, dp, ip, dp, dp, ip, dp]
+    lib.oracle_lu_cplx.restype = ctypes.c_int
+    lib.oracle_lu_cplx.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
+                                   ctypes.c_double, dp, ctypes.c_double, ctypes.c_int,
+                                   dp, ip, dp, dp, ip, dp]
+    lib.oracle_hsein_lu.restype = ctypes.c_int
+    lib.oracle_hsein_lu.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                    ctypes.c_int, dp, ctypes.c_int, ip, ip, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int]
     lib.oracle_q0_apply.restype = None
     lib.oracle_q0_apply.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
                                     ctypes.c_int, dp, ctypes.c_int, ctypes.c_int]
@@ -166,6 +177,68 @@ def hsein(H, wr, wi, B=None, log2_omega=LOG2_OMEGA_DEFAULT, robust=True, nthread
                               int(nthreads))
     if rc != 0:
         raise MemoryError("oracle_hsein failed to allocate")
+    if return_exponents:
+        return X, status, exps
+    return X, status
+
+
+def lu_real(H, lam, b, log2_omega=LOG2_OMEGA_DEFAULT, robust=True):
+    """The LU approach (Sec. 2.1) for one real shift: P (H - lam I) = L U,
+    L y = P b, U x = 2^-e y.  Returns (x, e, U packed by rows, L, piv,
+    replaced) with the true solution x * 2**e."""
+    H = _f64(H)
+    n = H.shape[0]
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty(n); U = np.empty(n * (n + 1) // 2); Lm = np.empty(n); work = np.empty(n)
+    piv = np.zeros(n, dtype=np.int32)
+    e = np.zeros(1, dtype=np.int32)
+    rep = _load().oracle_lu_real(n, _dp(H), n, float(lam), _dp(b), float(log2_omega),
+                                 int(bool(robust)), _dp(x), _ip(e), _dp(U), _dp(Lm), _ip(piv),
+                                 _dp(work))
+    return x, int(e[0]), U, Lm, piv, bool(rep)
+
+
+def lu_cplx(H, lam, b, log2_omega=LOG2_OMEGA_DEFAULT, robust=True):
+    """Complex counterpart of lu_real (lam and b complex)."""
+    H = _f64(H)
+    n = H.shape[0]
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    x = np.empty(n, dtype=np.complex128); U = np.empty(n * (n + 1) // 2, dtype=np.complex128)
+    Lm = np.empty(n, dtype=np.complex128); work = np.empty(n, dtype=np.complex128)
+    piv = np.zeros(n, dtype=np.int32)
+    e = np.zeros(1, dtype=np.int32)
+    lam = complex(lam)
+    rep = _load().oracle_lu_cplx(n, _dp(H), n, lam.real, lam.imag, _dp(b.view(np.float64)),
+                                 float(log2_omega), int(bool(robust)),
+                                 _dp(x.view(np.float64)), _ip(e), _dp(U.view(np.float64)),
+                                 _dp(Lm.view(np.float64)), _ip(piv), _dp(work.view(np.float64)))
+    return x, int(e[0]), U, Lm, piv, bool(rep)
+
+
+def hsein_lu(H, wr, wi, B=None, log2_omega=LOG2_OMEGA_DEFAULT, robust=True, nthreads=0,
+             return_exponents=False):
+    """hsein() with the LU approach of Sec. 2.1 in place of Henry's RQ solve
+    (the same outputs: unit-norm columns, status 0 converged / 1 not)."""
+    H = _f64(H)
+    n = H.shape[0]
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    wi = np.ascontiguousarray(wi, dtype=np.float64)
+    m = len(wr)
+    ncol = int(column_offsets(wi)[-1])
+    X = np.zeros((n, ncol), order="F")
+    status = np.zeros(m, dtype=np.int32)
+    exps = np.zeros(m, dtype=np.int32)
+    if B is None:
+        bptr = None
+    else:
+        B = _f64(B)
+        assert B.shape == (n, ncol)
+        bptr = _dp(B)
+    rc = _load().oracle_hsein_lu(n, _dp(H), n, m, _dp(wr), _dp(wi), bptr, n, _dp(X), n,
+                                 _ip(status), _ip(exps), float(log2_omega), int(bool(robust)),
+                                 int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle_hsein_lu failed to allocate")
     if return_exponents:
         return X, status, exps
     return X, status

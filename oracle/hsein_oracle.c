@@ -427,6 +427,276 @@ int oracle_hsein(int n, const double *H, int ldh, int m, const double *wr,
     return err ? -1 : 0;
 }
 
+/* ------------------------------------------- the LU comparison approach */
+
+/*
+ * The LU approach of LAPACK's inverse iteration (Sec. 2.1, the "LU
+ * Factorization" paragraph): P (H - lambda I) = L U with partial pivoting,
+ * then L y = P b and U x = 2^-e y, for the given starting vector b (the same
+ * system the RQ solve answers).  For a Hessenberg matrix the pivot search at
+ * step k is between two rows only: w, the row carried down (row k of
+ * H - lambda I once the earlier eliminations have acted on it), and row k+1
+ * of H - lambda I.  The one whose entry in column k has the larger magnitude
+ * becomes row k of U (ties keep w); the other is eliminated with the
+ * multiplier l_k = (its entry) / (the pivot), |l_k| <= 1, and is carried down.
+ * U is kept row-packed in Upk (row k holds columns k..n-1, n(n+1)/2 entries),
+ * l_k in L[k] and the interchange in piv[k].  A final pivot below
+ * eps ||H||_inf is replaced by eps ||H||_inf with its sign (the treatment of
+ * the RQ solve; every other pivot has magnitude >= |h(k+1,k)| > 0).
+ * Robustness (Sec. 4.1 applied to both substitutions, one exponent e for the
+ * whole vector): before y(k+1) -= l_k y(k) the vector is halved when
+ * |y(k+1)| + |y(k)| could exceed omega; the back substitution is the column
+ * form of Henry's solve, with ProtectDivision before each division by a
+ * pivot and ProtectUpdate before each column update.  On return x holds the
+ * scaled solution (true solution = x * 2^e).  work: n doubles.
+ * Returns 0, or 1 when the final pivot was replaced.
+ */
+static double packed_u(const double *Upk, int n, int i, int j)
+{
+    /* rows 0..i-1 hold n, n-1, ..., n-i+1 entries */
+    size_t off = (size_t)i * n - (size_t)i * (i - 1) / 2;
+    return Upk[off + (size_t)(j - i)];
+}
+
+int oracle_lu_real(int n, const double *H, int ldh, double lambda, const double *b,
+                   double log2_omega, int robust, double *x, int *e_out, double *Upk,
+                   double *L, int *piv, double *work)
+{
+    const double omega = ldexp(1.0, (int)log2_omega);
+    const double hnorm = oracle_hnorm_inf(n, H, ldh);
+    double *w = work;
+    int e = 0, replaced = 0;
+
+    /* factorization */
+    for (int j = 0; j < n; ++j) w[j] = H[(size_t)j * ldh] - (j == 0 ? lambda : 0.0);
+    for (int k = 0; k + 1 < n; ++k) {
+        size_t off = (size_t)k * n - (size_t)k * (k - 1) / 2;
+        double t_k = H[k + 1 + (size_t)k * ldh];  /* row k+1 of H - lambda I, column k */
+        int swap = fabs(t_k) > fabs(w[k]);
+        piv[k] = swap;
+        double pivot = swap ? t_k : w[k];
+        double other = swap ? w[k] : t_k;
+        double l = other / pivot;
+        L[k] = l;
+        Upk[off] = pivot;
+        for (int j = k + 1; j < n; ++j) {
+            double t = H[k + 1 + (size_t)j * ldh] - (j == k + 1 ? lambda : 0.0);
+            double u = swap ? t : w[j];
+            double o = swap ? w[j] : t;
+            Upk[off + (size_t)(j - k)] = u;
+            w[j] = o - l * u;
+        }
+    }
+    {
+        size_t off = (size_t)(n - 1) * n - (size_t)(n - 1) * (n - 2) / 2;
+        double r = w[n - 1];
+        double small = ORACLE_EPS * hnorm;
+        if (fabs(r) < small) {
+            r = copysign(small, r);
+            replaced = 1;
+        }
+        Upk[off] = r;
+    }
+
+    /* forward substitution L y = P b (y kept in x) */
+    for (int i = 0; i < n; ++i) x[i] = b[i];
+    for (int k = 0; k + 1 < n; ++k) {
+        if (piv[k]) {
+            double t = x[k];
+            x[k] = x[k + 1];
+            x[k + 1] = t;
+        }
+        if (robust && fabs(x[k + 1]) > omega - fabs(x[k])) {
+            for (int i = 0; i < n; ++i) x[i] = ldexp(x[i], -1);
+            e += 1;
+        }
+        x[k + 1] -= L[k] * x[k];
+    }
+
+    /* back substitution U x = 2^-e y, column by column */
+    for (int i = n - 1; i >= 0; --i) {
+        double uii = packed_u(Upk, n, i, i);
+        if (robust) {
+            int q = protect_division(fabs(x[i]), fabs(uii), omega);
+            if (q) {
+                for (int j = 0; j < n; ++j) x[j] = ldexp(x[j], -q);
+                e += q;
+            }
+        }
+        x[i] /= uii;
+        if (i == 0) break;
+        if (robust) {
+            double umax = 0.0, xmax = 0.0;
+            for (int j = 0; j < i; ++j) {
+                double u = fabs(packed_u(Upk, n, j, i));
+                if (u > umax) umax = u;
+                if (fabs(x[j]) > xmax) xmax = fabs(x[j]);
+            }
+            int q = protect_update(xmax, umax, fabs(x[i]), omega);
+            if (q) {
+                for (int j = 0; j < n; ++j) x[j] = ldexp(x[j], -q);
+                e += q;
+            }
+        }
+        for (int j = 0; j < i; ++j) x[j] -= x[i] * packed_u(Upk, n, j, i);
+    }
+    *e_out = e;
+    return replaced;
+}
+
+static size_t packed_off(int n, int i) { return (size_t)i * n - (size_t)i * (i - 1) / 2; }
+
+/* the complex counterpart (Sec. 4.3): lambda and b complex, H real; pivots
+ * compared by modulus, divisions by Smith's method */
+int oracle_lu_cplx(int n, const double *H, int ldh, double lre, double lim, const zdouble *b,
+                   double log2_omega, int robust, zdouble *x, int *e_out, zdouble *Upk,
+                   zdouble *L, int *piv, zdouble *work)
+{
+    const double omega = ldexp(1.0, (int)log2_omega);
+    const double hnorm = oracle_hnorm_inf(n, H, ldh);
+    const zdouble lambda = lre + I * lim;
+    zdouble *w = work;
+    int e = 0, replaced = 0;
+
+    for (int j = 0; j < n; ++j) w[j] = H[(size_t)j * ldh] - (j == 0 ? lambda : 0.0);
+    for (int k = 0; k + 1 < n; ++k) {
+        size_t off = packed_off(n, k);
+        zdouble t_k = H[k + 1 + (size_t)k * ldh];
+        int swap = zabs(t_k) > zabs(w[k]);
+        piv[k] = swap;
+        zdouble pivot = swap ? t_k : w[k];
+        zdouble other = swap ? w[k] : t_k;
+        zdouble l = zdiv_smith(other, pivot);
+        L[k] = l;
+        Upk[off] = pivot;
+        for (int j = k + 1; j < n; ++j) {
+            zdouble t = H[k + 1 + (size_t)j * ldh] - (j == k + 1 ? lambda : 0.0);
+            zdouble u = swap ? t : w[j];
+            zdouble o = swap ? w[j] : t;
+            Upk[off + (size_t)(j - k)] = u;
+            w[j] = o - l * u;
+        }
+    }
+    {
+        zdouble r = w[n - 1];
+        double small = ORACLE_EPS * hnorm;
+        double a = zabs(r);
+        if (a < small) {
+            r = (a > 0.0) ? r * (small / a) : small;
+            replaced = 1;
+        }
+        Upk[packed_off(n, n - 1)] = r;
+    }
+    for (int i = 0; i < n; ++i) x[i] = b[i];
+    for (int k = 0; k + 1 < n; ++k) {
+        if (piv[k]) {
+            zdouble t = x[k];
+            x[k] = x[k + 1];
+            x[k + 1] = t;
+        }
+        if (robust && zabs(x[k + 1]) > omega - zabs(x[k])) {
+            for (int i = 0; i < n; ++i) x[i] = ldexp(creal(x[i]), -1) + I * ldexp(cimag(x[i]), -1);
+            e += 1;
+        }
+        x[k + 1] -= L[k] * x[k];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        zdouble uii = Upk[packed_off(n, i)];
+        if (robust) {
+            int q = protect_division(zabs(x[i]), zabs(uii), omega);
+            if (q) {
+                for (int j = 0; j < n; ++j) x[j] = ldexp(creal(x[j]), -q) + I * ldexp(cimag(x[j]), -q);
+                e += q;
+            }
+        }
+        x[i] = zdiv_smith(x[i], uii);
+        if (i == 0) break;
+        if (robust) {
+            double umax = 0.0, xmax = 0.0;
+            for (int j = 0; j < i; ++j) {
+                double u = zabs(Upk[packed_off(n, j) + (size_t)(i - j)]);
+                if (u > umax) umax = u;
+                if (zabs(x[j]) > xmax) xmax = zabs(x[j]);
+            }
+            int q = protect_update(xmax, umax, zabs(x[i]), omega);
+            if (q) {
+                for (int j = 0; j < n; ++j) x[j] = ldexp(creal(x[j]), -q) + I * ldexp(cimag(x[j]), -q);
+                e += q;
+            }
+        }
+        for (int j = 0; j < i; ++j) x[j] -= x[i] * Upk[packed_off(n, j) + (size_t)(i - j)];
+    }
+    *e_out = e;
+    return replaced;
+}
+
+/*
+ * Driver of the LU approach for m shifts, with the interface and outputs of
+ * oracle_hsein (unit-norm columns, Varah's test with the exponent, zeroed
+ * columns where it fails).  There is no Givens backtransform: U x = y solves
+ * for x directly.  Each shift needs a packed U of n(n+1)/2 entries.
+ */
+int oracle_hsein_lu(int n, const double *H, int ldh, int m, const double *wr,
+                    const double *wi, const double *B, int ldb, double *X, int ldx,
+                    int *status, int *exps, double log2_omega, int robust, int nthreads)
+{
+    int *col = (int *)malloc(sizeof(int) * (size_t)(m + 1));
+    if (!col) return -1;
+    col[0] = 0;
+    for (int l = 0; l < m; ++l) col[l + 1] = col[l] + (wi[l] != 0.0 ? 2 : 1);
+    const double hnorm = oracle_hnorm_inf(n, H, ldh);
+    const double rho = ORACLE_EPS * hnorm;
+    const double log2_thresh = -log2(10.0 * n * hnorm * ORACLE_EPS);
+    const size_t np = (size_t)n * (n + 1) / 2;
+    int err = 0;
+
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+#endif
+    for (int l = 0; l < m; ++l) {
+        int c0 = col[l], e = 0;
+        int *piv = (int *)malloc(sizeof(int) * (size_t)n);
+        if (!piv) { err |= 1; continue; }
+        if (wi[l] == 0.0) {
+            double *b = (double *)malloc(sizeof(double) * ((size_t)n * 4 + np));
+            if (!b) { free(piv); err |= 1; continue; }
+            double *x = b + n, *Lm = b + 2 * (size_t)n, *work = b + 3 * (size_t)n;
+            double *Upk = b + 4 * (size_t)n;
+            for (int i = 0; i < n; ++i) b[i] = B ? B[i + (size_t)c0 * ldb] : rho;
+            double b2 = scaled_nrm2(n, b, 1);
+            oracle_lu_real(n, H, ldh, wr[l], b, log2_omega, robust, x, &e, Upk, Lm, piv, work);
+            double nrm = scaled_nrm2(n, x, 1);
+            int conv = (nrm > 0.0) && (log2(nrm) + e - log2(b2) > log2_thresh);
+            for (int i = 0; i < n; ++i) X[i + (size_t)c0 * ldx] = conv ? x[i] / nrm : 0.0;
+            status[l] = conv ? 0 : 1;
+            free(b);
+        } else {
+            zdouble *b = (zdouble *)malloc(sizeof(zdouble) * ((size_t)n * 4 + np));
+            if (!b) { free(piv); err |= 1; continue; }
+            zdouble *x = b + n, *Lm = b + 2 * (size_t)n, *work = b + 3 * (size_t)n;
+            zdouble *Upk = b + 4 * (size_t)n;
+            for (int i = 0; i < n; ++i)
+                b[i] = B ? (B[i + (size_t)c0 * ldb] + I * B[i + (size_t)(c0 + 1) * ldb]) : rho;
+            double b2 = scaled_nrm2_z(n, b);
+            oracle_lu_cplx(n, H, ldh, wr[l], wi[l], b, log2_omega, robust, x, &e, Upk, Lm, piv,
+                           work);
+            double nrm = scaled_nrm2_z(n, x);
+            int conv = (nrm > 0.0) && (log2(nrm) + e - log2(b2) > log2_thresh);
+            for (int i = 0; i < n; ++i) {
+                X[i + (size_t)c0 * ldx] = conv ? creal(x[i]) / nrm : 0.0;
+                X[i + (size_t)(c0 + 1) * ldx] = conv ? cimag(x[i]) / nrm : 0.0;
+            }
+            status[l] = conv ? 0 : 1;
+            free(b);
+        }
+        free(piv);
+        if (exps) exps[l] = e;
+    }
+    free(col);
+    return err ? -1 : 0;
+}
+
 /* z = Q0 x for every column (the map from eigenvectors of H to those of A,
  * Sec. 1).  Plain triple loop, OpenMP over columns. */
 void oracle_q0_apply(int n, const double *Q, int ldq, int ncol, const double *X,

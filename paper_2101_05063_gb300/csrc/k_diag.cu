@@ -119,15 +119,20 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
     auto lb2 = [&](double a, double b) { return CPLX ? max(lbound(a), lbound(b)) + 1 : lbound(a); };
 
     double vr[RPL], vi[RPL], xr[RPL], xi[RPL];
+    // the tile rows of the working column and of x (global memory is not
+    // written before phase 1 ends, so a re-run of the sweep reloads them)
+    auto load_slots = [&]() {
 #pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-        const int i = r + LPS * t;
-        const bool ok = qok && i < bt;
-        vr[t] = ok ? R[p0 + i + (size_t)col * L.ldw] : 0.0;
-        xr[t] = ok ? X[p0 + i + (size_t)col * L.ldw] : 0.0;
-        vi[t] = (CPLX && ok) ? R[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
-        xi[t] = (CPLX && ok) ? X[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
-    }
+        for (int t = 0; t < RPL; ++t) {
+            const int i = r + LPS * t;
+            const bool ok = qok && i < bt;
+            vr[t] = ok ? R[p0 + i + (size_t)col * L.ldw] : 0.0;
+            xr[t] = ok ? X[p0 + i + (size_t)col * L.ldw] : 0.0;
+            vi[t] = (CPLX && ok) ? R[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
+            xi[t] = (CPLX && ok) ? X[p0 + i + (size_t)(col + 1) * L.ldw] : 0.0;
+        }
+    };
+    load_slots();
     const int eB0 = qok ? eB[q] : 0;
     int e = eB0;
     auto xmax_bound = [&]() {
@@ -157,208 +162,247 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
     // above are then updated: the slot that holds row k-1 (the next pivot) at
     // once, the slots below it one step later, in the same instruction stream
     // as the next rotation, whose dependency chain would otherwise leave the
-    // FP64 pipe idle.  The unscaled, unprotected rotation is the fast path;
-    // when any group needs the overflow scaling of phi or a protection step
-    // (ProtectDivision / ProtectUpdate), the whole warp recomputes the step
-    // the careful way, which gives the same values whenever nothing rescales.
+    // FP64 pipe idle.
+    // The sweep runs first with the unscaled, unprotected rotation and no
+    // per-step decision: each step only records, with integer tests of
+    // exponent fields, whether the overflow scaling of phi or a protection
+    // step (ProtectDivision / ProtectUpdate) could be needed (conservative
+    // tests).  If any lane recorded one, the tile's rows are reloaded and the
+    // sweep runs again the careful way, where every step decides for the
+    // whole warp and recomputes the rotation with scaling and protection
+    // when needed; that gives the first run's values whenever nothing
+    // rescales.
     double* s_d = sm + 5 * br;   // h(i,i) - Re(lambda): the shifted diagonal
     double* s_h2 = sm + 6 * br;  // h(k,k-1)^2, the rotation's constant term
     for (int i = r; i + 1 < bt; i += LPS) s_d[i] = Hs[(i + 1) * br + i] - lre;
     for (int k = r; k < bt; k += LPS) s_h2[k] = Hs[(size_t)k * br + k] * Hs[(size_t)k * br + k];
     __syncwarp();
     const int role = r;
-    // the rotation waiting for the slots below the pivot slot (identity at first)
-    double p_ar = 0.0, p_ai = 0.0, p_bR = 0.0, p_bI = 0.0, p_cr = 0.0, p_ci = 0.0, p_s = 1.0;
-    const double* p_col = Hs;
-
-    auto apply_pending = [&](auto NPc) {
-        constexpr int NP = decltype(NPc)::value;
-#pragma unroll
-        for (int t = 0; t < NP; ++t) {
-            const double tr = p_col[r + LPS * t];
-            if (CPLX) {
-                xr[t] = fma(-p_ar, vr[t], fma(p_ai, vi[t], fma(p_bR, tr, xr[t])));
-                xi[t] = fma(-p_ar, vi[t], fma(-p_ai, vr[t], fma(p_bI, tr, xi[t])));
-                const double nvr = fma(p_cr, tr, p_s * vr[t]);
-                const double nvi = fma(p_ci, tr, p_s * vi[t]);
-                vr[t] = nvr;
-                vi[t] = nvi;
-            } else {
-                xr[t] = fma(-p_ar, vr[t], fma(p_bR, tr, xr[t]));
-                vr[t] = fma(p_cr, tr, p_s * vr[t]);
-            }
-        }
+    // fast-path exponent bound, integer only: floor(log2|v|) + 1 for normal v;
+    // for zero and subnormal v the bound of the smallest normal number
+    auto lbf = [](double v) {
+        const int ex = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+        return max(ex, 1) - 1022;
     };
+    auto lbf2 = [&](double a, double b) { return CPLX ? max(lbf(a), lbf(b)) + 1 : lbf(a); };
 
-    // one step; TK = slot of the pivot row k, PEEL = the step with k % LPS == 0
-    // (row k-1 then sits in slot TK-1)
-    auto step = [&](auto TKc, auto PEELc, int rk) {
-        constexpr int TK = decltype(TKc)::value;
-        constexpr bool PEEL = decltype(PEELc)::value;
-        constexpr int US = PEEL ? TK - 1 : TK;  // slot of row k-1
-        const int k = LPS * TK + rk;
-        const int src = gbase | rk;
-        const double vkr = __shfl_sync(kFull, vr[TK], src);
-        const double xkr = __shfl_sync(kFull, xr[TK], src);
-        const double vki = CPLX ? __shfl_sync(kFull, vi[TK], src) : 0.0;
-        const double xki = CPLX ? __shfl_sync(kFull, xi[TK], src) : 0.0;
-        const double* Hcol = Hs + (size_t)k * br;  // h(:, k-1) of the tile
-        const double hs = Hcol[k];                 // h(k, k-1)
-        apply_pending(std::integral_constant<int, TK>{});
+    auto sweep = [&](auto FASTc) -> bool {
+        constexpr bool FAST = decltype(FASTc)::value;
+        bool bad = false;  // FAST: some step may have needed the careful treatment
+        // the rotation waiting for the slots below the pivot slot (identity at first)
+        double p_ar = 0.0, p_ai = 0.0, p_bR = 0.0, p_bI = 0.0, p_cr = 0.0, p_ci = 0.0, p_s = 1.0;
+        const double* p_col = Hs;
 
-        // rotation (eq. "givens" / "cgivens"): 1/phi = rsqrt(h^2 + |v|^2)
-        const double h2 = s_h2[k];
-        const double ss = CPLX ? fma(vkr, vkr, fma(vki, vki, h2)) : fma(vkr, vkr, h2);
-        const double rr = rsqrt(ss);
-        double m1;
-        if (CPLX)
-            m1 = role == 0 ? vkr : role == 1 ? vki : role == 2 ? -hs : role == 3 ? xkr : xki;
-        else
-            m1 = role == 0 ? vkr : role == 1 ? -hs : xkr;
-        const double f1 = m1 * rr;
-        double cr = __shfl_sync(kFull, f1, gbase);
-        double ci = CPLX ? __shfl_sync(kFull, f1, gbase | 1) : 0.0;
-        double s = __shfl_sync(kFull, f1, gbase | (CPLX ? 2 : 1));
-        double xkr1 = __shfl_sync(kFull, f1, gbase | (CPLX ? 3 : 2));
-        double xki1 = CPLX ? __shfl_sync(kFull, f1, gbase | 4) : 0.0;
-        // a = x(k) conj(c), b = x(k) s
-        double f2;
-        if (CPLX) {
-            const double u0 = (role & 1) ? xki1 : xkr1;
-            const double v0 = role < 2 ? cr : s;
-            const double u1 = role == 0 ? xki1 : role == 1 ? -xkr1 : 0.0;
-            const double v1 = role < 2 ? ci : 0.0;
-            f2 = fma(u0, v0, u1 * v1);
-        } else {
-            f2 = xkr1 * (role == 0 ? cr : s);
-        }
-        double ar = __shfl_sync(kFull, f2, gbase);
-        double ai = CPLX ? __shfl_sync(kFull, f2, gbase | 1) : 0.0;
-        double bR = __shfl_sync(kFull, f2, gbase | (CPLX ? 2 : 1));
-        double bI = CPLX ? __shfl_sync(kFull, f2, gbase | 3) : 0.0;
-
-        int eh = max(lbound(hs), lbound(vkr));
-        if (CPLX) eh = max(eh, lbound(vki));
-        bool need = eh > 500 || eh < -500;
-        int nb = 0;
-        if (robust) {
-            const int sq = lb2(xkr, xki) + lbound(rr) - om;  // ProtectDivision
-            nb = max(bx, LRb + lb2(xkr1, xki1)) + 1;          // ProtectUpdate
-            need = need || sq > 0 || nb > om;
-        }
-        if (__any_sync(kFull, need)) {
-            // careful step: phi with a power-of-two prescale against
-            // overflow, then the protections with rescaling of x
-            double hsc = hs, vsr = vkr, vsi = vki, sc = 1.0;
-            if (eh > 500 || eh < -500) {
-                sc = exact_pow2(min(-eh, 1023));  // eh in [-1073, 1024]: 2^-eh, finite
-                hsc *= sc;
-                vsr *= sc;
-                if (CPLX) vsi *= sc;
+        auto apply_pending = [&](auto NPc) {
+            constexpr int NP = decltype(NPc)::value;
+#pragma unroll
+            for (int t = 0; t < NP; ++t) {
+                const double tr = p_col[r + LPS * t];
+                if (CPLX) {
+                    xr[t] = fma(-p_ar, vr[t], fma(p_ai, vi[t], fma(p_bR, tr, xr[t])));
+                    xi[t] = fma(-p_ar, vi[t], fma(-p_ai, vr[t], fma(p_bI, tr, xi[t])));
+                    const double nvr = fma(p_cr, tr, p_s * vr[t]);
+                    const double nvi = fma(p_ci, tr, p_s * vi[t]);
+                    vr[t] = nvr;
+                    vi[t] = nvi;
+                } else {
+                    xr[t] = fma(-p_ar, vr[t], fma(p_bR, tr, xr[t]));
+                    vr[t] = fma(p_cr, tr, p_s * vr[t]);
+                }
             }
-            const double ss2 =
-                CPLX ? fma(vsr, vsr, fma(vsi, vsi, hsc * hsc)) : fma(vsr, vsr, hsc * hsc);
-            const double rr2 = rsqrt(ss2);
-            cr = vsr * rr2;
-            s = -hsc * rr2;
-            ci = CPLX ? vsi * rr2 : 0.0;
-            const double rinv = rr2 * sc;
-            xkr1 = xkr;
-            xki1 = xki;
-            if (robust) {
-                const int sq = lb2(xkr1, xki1) + lbound(rinv) - om;
-                if (sq > 0) rescale(sq, xkr1, xki1);
+        };
+
+        // one step; TK = slot of the pivot row k, PEEL = the step with k % LPS == 0
+        // (row k-1 then sits in slot TK-1)
+        auto step = [&](auto TKc, auto PEELc, int rk) {
+            constexpr int TK = decltype(TKc)::value;
+            constexpr bool PEEL = decltype(PEELc)::value;
+            constexpr int US = PEEL ? TK - 1 : TK;  // slot of row k-1
+            const int k = LPS * TK + rk;
+            const int src = gbase | rk;
+            const double vkr = __shfl_sync(kFull, vr[TK], src);
+            const double xkr = __shfl_sync(kFull, xr[TK], src);
+            const double vki = CPLX ? __shfl_sync(kFull, vi[TK], src) : 0.0;
+            const double xki = CPLX ? __shfl_sync(kFull, xi[TK], src) : 0.0;
+            const double* Hcol = Hs + (size_t)k * br;  // h(:, k-1) of the tile
+            const double hs = Hcol[k];                 // h(k, k-1)
+            apply_pending(std::integral_constant<int, TK>{});
+
+            // rotation (eq. "givens" / "cgivens"): 1/phi = rsqrt(h^2 + |v|^2)
+            const double h2 = s_h2[k];
+            const double ss = CPLX ? fma(vkr, vkr, fma(vki, vki, h2)) : fma(vkr, vkr, h2);
+            const double rr = rsqrt(ss);
+            double m1;
+            if (CPLX)
+                m1 = role == 0 ? vkr : role == 1 ? vki : role == 2 ? -hs : role == 3 ? xkr : xki;
+            else
+                m1 = role == 0 ? vkr : role == 1 ? -hs : xkr;
+            const double f1 = m1 * rr;
+            double cr = __shfl_sync(kFull, f1, gbase);
+            double ci = CPLX ? __shfl_sync(kFull, f1, gbase | 1) : 0.0;
+            double s = __shfl_sync(kFull, f1, gbase | (CPLX ? 2 : 1));
+            double xkr1 = __shfl_sync(kFull, f1, gbase | (CPLX ? 3 : 2));
+            double xki1 = CPLX ? __shfl_sync(kFull, f1, gbase | 4) : 0.0;
+            // a = x(k) conj(c), b = x(k) s
+            double f2;
+            if (CPLX) {
+                const double u0 = (role & 1) ? xki1 : xkr1;
+                const double v0 = role < 2 ? cr : s;
+                const double u1 = role == 0 ? xki1 : role == 1 ? -xkr1 : 0.0;
+                const double v1 = role < 2 ? ci : 0.0;
+                f2 = fma(u0, v0, u1 * v1);
+            } else {
+                f2 = xkr1 * (role == 0 ? cr : s);
             }
-            xkr1 *= rinv;
-            if (CPLX) xki1 *= rinv;
-            if (robust) {
-                const int lx = lb2(xkr1, xki1);
-                int nb2 = max(bx, LRb + lx) + 1;
-                const bool refine = nb2 > om;
-                // the exact maximum is a shuffle over the group: every lane of
-                // the warp takes part whenever any group needs it
-                if (__any_sync(kFull, refine)) {
-                    const int bexact = xmax_bound();
-                    if (refine) {
-                        bx = max(bexact, lx);
-                        nb2 = max(bx, LRb + lx) + 1;
-                        if (nb2 > om) {
-                            rescale(nb2 - om, xkr1, xki1);
-                            nb2 = om;
+            double ar = __shfl_sync(kFull, f2, gbase);
+            double ai = CPLX ? __shfl_sync(kFull, f2, gbase | 1) : 0.0;
+            double bR = __shfl_sync(kFull, f2, gbase | (CPLX ? 2 : 1));
+            double bI = CPLX ? __shfl_sync(kFull, f2, gbase | 3) : 0.0;
+
+            if constexpr (FAST) {
+                // integer tests only: phi^2 outside [2^-1000, 2^1000] (the
+                // squares need the power-of-two prescale), |x(k)/phi| or the
+                // update bound at or above 2^omega (a protection step)
+                const int es = (int)((__double_as_longlong(ss) >> 52) & 0x7FF);
+                bool need = es < 23 || es > 2022;
+                if (robust) {
+                    const int lx = lbf2(xkr1, xki1);
+                    const int nb = max(bx, LRb + lx) + 1;
+                    need = need || lx >= om || nb > om;
+                    bx = nb;
+                }
+                bad = bad || need;
+            } else {
+                int eh = max(lbound(hs), lbound(vkr));
+                if (CPLX) eh = max(eh, lbound(vki));
+                bool need = eh > 500 || eh < -500;
+                int nb = 0;
+                if (robust) {
+                    const int sq = lb2(xkr, xki) + lbound(rr) - om;  // ProtectDivision
+                    nb = max(bx, LRb + lb2(xkr1, xki1)) + 1;          // ProtectUpdate
+                    need = need || sq > 0 || nb > om;
+                }
+                if (__any_sync(kFull, need)) {
+                    // careful step: phi with a power-of-two prescale against
+                    // overflow, then the protections with rescaling of x
+                    double hsc = hs, vsr = vkr, vsi = vki, sc = 1.0;
+                    if (eh > 500 || eh < -500) {
+                        sc = exact_pow2(min(-eh, 1023));  // eh in [-1073, 1024]: 2^-eh, finite
+                        hsc *= sc;
+                        vsr *= sc;
+                        if (CPLX) vsi *= sc;
+                    }
+                    const double ss2 =
+                        CPLX ? fma(vsr, vsr, fma(vsi, vsi, hsc * hsc)) : fma(vsr, vsr, hsc * hsc);
+                    const double rr2 = rsqrt(ss2);
+                    cr = vsr * rr2;
+                    s = -hsc * rr2;
+                    ci = CPLX ? vsi * rr2 : 0.0;
+                    const double rinv = rr2 * sc;
+                    xkr1 = xkr;
+                    xki1 = xki;
+                    if (robust) {
+                        const int sq = lb2(xkr1, xki1) + lbound(rinv) - om;
+                        if (sq > 0) rescale(sq, xkr1, xki1);
+                    }
+                    xkr1 *= rinv;
+                    if (CPLX) xki1 *= rinv;
+                    if (robust) {
+                        const int lx = lb2(xkr1, xki1);
+                        int nb2 = max(bx, LRb + lx) + 1;
+                        const bool refine = nb2 > om;
+                        // the exact maximum is a shuffle over the group: every lane of
+                        // the warp takes part whenever any group needs it
+                        if (__any_sync(kFull, refine)) {
+                            const int bexact = xmax_bound();
+                            if (refine) {
+                                bx = max(bexact, lx);
+                                nb2 = max(bx, LRb + lx) + 1;
+                                if (nb2 > om) {
+                                    rescale(nb2 - om, xkr1, xki1);
+                                    nb2 = om;
+                                }
+                            }
                         }
+                        bx = nb2;
+                    }
+                    ar = CPLX ? fma(xkr1, cr, xki1 * ci) : xkr1 * cr;
+                    ai = CPLX ? fma(xki1, cr, -xkr1 * ci) : 0.0;
+                    bR = xkr1 * s;
+                    bI = CPLX ? xki1 * s : 0.0;
+                } else if (robust) {
+                    bx = nb;
+                }
+            }
+            if (L.compact) {
+                // the canonical rotation (what compact storage recovers); a and b
+                // do not change with the flip
+                const unsigned long long f = canon_mask<CPLX>(cr, ci, s);
+                cr = flip_if(cr, f);
+                ci = flip_if(ci, f);
+                s = flip_if(s, f);
+                xkr1 = flip_if(xkr1, f);
+                xki1 = flip_if(xki1, f);
+            }
+            // row k is final
+            if (r == rk) {
+                xr[TK] = xkr1;
+                if (CPLX) xi[TK] = xki1;
+                s_cr[k] = cr;
+                if (CPLX) s_ci[k] = ci;
+                s_s[k] = s;
+            }
+            // slot US now (it holds row k-1, whose t entry is the shifted
+            // diagonal h(k-1,k-1) - lambda): x -= a v - b t, v = c t + s v
+            {
+                const int i = r + LPS * US;
+                const bool dg = i == k - 1;
+                if (PEEL || r < rk) {
+                    const double tr = dg ? s_d[i] : Hcol[i];
+                    if (CPLX) {
+                        const double dli = dg ? lim : 0.0;  // t = tr - i lim on the diagonal
+                        xr[US] = fma(bI, dli, fma(-ar, vr[US], fma(ai, vi[US], fma(bR, tr, xr[US]))));
+                        xi[US] = fma(-bR, dli, fma(-ar, vi[US], fma(-ai, vr[US], fma(bI, tr, xi[US]))));
+                        const double nvr = fma(ci, dli, fma(cr, tr, s * vr[US]));
+                        const double nvi = fma(-cr, dli, fma(ci, tr, s * vi[US]));
+                        vr[US] = nvr;
+                        vi[US] = nvi;
+                    } else {
+                        xr[US] = fma(-ar, vr[US], fma(bR, tr, xr[US]));
+                        vr[US] = fma(cr, tr, s * vr[US]);
                     }
                 }
-                bx = nb2;
             }
-            ar = CPLX ? fma(xkr1, cr, xki1 * ci) : xkr1 * cr;
-            ai = CPLX ? fma(xki1, cr, -xkr1 * ci) : 0.0;
-            bR = xkr1 * s;
-            bI = CPLX ? xki1 * s : 0.0;
-        } else if (robust) {
-            bx = nb;
-        }
+            // the slots below US take this rotation at the next step
+            p_ar = ar;
+            p_ai = ai;
+            p_bR = bR;
+            p_bI = bI;
+            p_cr = cr;
+            p_ci = ci;
+            p_s = s;
+            p_col = Hcol;
+        };
 
-        if (L.compact) {
-            // the canonical rotation (what compact storage recovers); a and b
-            // do not change with the flip
-            const unsigned long long f = canon_mask<CPLX>(cr, ci, s);
-            cr = flip_if(cr, f);
-            ci = flip_if(ci, f);
-            s = flip_if(s, f);
-            xkr1 = flip_if(xkr1, f);
-            xki1 = flip_if(xki1, f);
-        }
-        // row k is final
-        if (r == rk) {
-            xr[TK] = xkr1;
-            if (CPLX) xi[TK] = xki1;
-            s_cr[k] = cr;
-            if (CPLX) s_ci[k] = ci;
-            s_s[k] = s;
-        }
-        // slot US now (it holds row k-1, whose t entry is the shifted
-        // diagonal h(k-1,k-1) - lambda): x -= a v - b t, v = c t + s v
-        {
-            const int i = r + LPS * US;
-            const bool dg = i == k - 1;
-            if (PEEL || r < rk) {
-                const double tr = dg ? s_d[i] : Hcol[i];
-                if (CPLX) {
-                    const double dli = dg ? lim : 0.0;  // t = tr - i lim on the diagonal
-                    xr[US] = fma(bI, dli, fma(-ar, vr[US], fma(ai, vi[US], fma(bR, tr, xr[US]))));
-                    xi[US] = fma(-bR, dli, fma(-ar, vi[US], fma(-ai, vr[US], fma(bI, tr, xi[US]))));
-                    const double nvr = fma(ci, dli, fma(cr, tr, s * vr[US]));
-                    const double nvi = fma(-cr, dli, fma(ci, tr, s * vi[US]));
-                    vr[US] = nvr;
-                    vi[US] = nvi;
-                } else {
-                    xr[US] = fma(-ar, vr[US], fma(bR, tr, xr[US]));
-                    vr[US] = fma(cr, tr, s * vr[US]);
-                }
+        auto block = [&](auto TKc) {
+            constexpr int TK = decltype(TKc)::value;
+            for (int rk = LPS - 1; rk >= 1; --rk) {
+                if (LPS * TK + rk >= bt) continue;
+                step(TKc, std::false_type{}, rk);
             }
-        }
-        // the slots below US take this rotation at the next step
-        p_ar = ar;
-        p_ai = ai;
-        p_bR = bR;
-        p_bI = bI;
-        p_cr = cr;
-        p_ci = ci;
-        p_s = s;
-        p_col = Hcol;
+            if constexpr (TK >= 1) {
+                if (LPS * TK < bt) step(TKc, std::true_type{}, 0);
+            }
+        };
+        static_down<RPL - 1>(block);
+        return bad;
     };
-
-    auto block = [&](auto TKc) {
-        constexpr int TK = decltype(TKc)::value;
-        for (int rk = LPS - 1; rk >= 1; --rk) {
-            if (LPS * TK + rk >= bt) continue;
-            step(TKc, std::false_type{}, rk);
-        }
-        if constexpr (TK >= 1) {
-            if (LPS * TK < bt) step(TKc, std::true_type{}, 0);
-        }
-    };
-    static_down<RPL - 1>(block);
+    if (__any_sync(kFull, sweep(std::true_type{}))) {
+        load_slots();
+        e = eB0;
+        bx = xmax_bound();
+        sweep(std::false_type{});
+    }
 
     // ---------------- row 0: left rotation or final pivot ----------------
     {

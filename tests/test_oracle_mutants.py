@@ -42,6 +42,13 @@ MUTANTS = {
     "hnorm_column_sums": ("for (int j = j0; j < n; ++j) s += fabs(H[i + (size_t)j * ldh]);",
                           "for (int j = j0; j < n; ++j) s += fabs(H[j + (size_t)i * ldh]);"),
     "hnorm_subdiagonal_dropped": ("int j0 = i > 0 ? i - 1 : 0;", "int j0 = i;"),
+    "lu_pivot_inverted": ("        int swap = fabs(t_k) > fabs(w[k]);", "        int swap = fabs(t_k) < fabs(w[k]);"),
+    "lu_elimination_sign": ("            w[j] = o - l * u;\n        }\n    }\n    {\n        size_t off",
+                            "            w[j] = o + l * u;\n        }\n    }\n    {\n        size_t off"),
+    "lu_forward_interchange_dropped": ("        if (piv[k]) {\n            double t = x[k];", "        if (0) {\n            double t = x[k];"),
+    "lu_back_update_sign": ("        for (int j = 0; j < i; ++j) x[j] -= x[i] * packed_u(Upk, n, j, i);",
+                            "        for (int j = 0; j < i; ++j) x[j] += x[i] * packed_u(Upk, n, j, i);"),
+    "lu_forward_protection_off": ("        if (robust && fabs(x[k + 1]) > omega - fabs(x[k])) {", "        if (0) {"),
 }
 
 # pin tests (function, args) run against each mutant
@@ -61,6 +68,12 @@ PIN_CALLS = [
     (pins.test_default_starting_vector_is_rho_e, ()),
     (pins.test_exact_eigenvalue_pivot_replacement, ()),
     (pins.test_bad_system_h2_through_the_driver, ()),
+    (pins.test_lu_real_solve_matches_exact_rational, (8, 1)),
+    (pins.test_lu_real_solve_matches_exact_rational, (3, 2)),
+    (pins.test_lu_complex_solve_matches_exact_rational, (5,)),
+    (pins.test_lu_factors_reproduce_the_shifted_matrix_with_bounded_multipliers, (False,)),
+    (pins.test_lu_scaling_is_needed_and_exact, ()),
+    (pins.test_lu_companion_eigenvectors_closed_form, ()),
 ]
 
 

@@ -388,6 +388,154 @@ def test_bad_system_h2_through_the_driver():
     assert residual(H, 2.0, X[:, 0]) <= 100 * n * EPS
 
 
+# ------------------------------------------------- the LU approach (Sec. 2.1)
+
+def _lu_factors(n, U, Lm, piv):
+    """Dense P, L, U of P (H - lambda I) = L U from the oracle's packed output:
+    row k of U holds columns k..n-1; step k exchanges rows k and k+1 when
+    piv[k] and eliminates row k+1 with multiplier Lm[k]."""
+    dt = U.dtype
+    Ud = np.zeros((n, n), dtype=dt)
+    off = 0
+    for k in range(n):
+        Ud[k, k:] = U[off:off + n - k]
+        off += n - k
+    # P and L as products of elementary steps: M_{n-2} P_{n-2} ... M_0 P_0 (H - lam I) = U
+    Minv = np.eye(n, dtype=dt)  # accumulates (M P)^-1 = P^T M^-1 in order
+    for k in range(n - 1):
+        Pk = np.eye(n, dtype=dt)
+        if piv[k]:
+            Pk[[k, k + 1]] = Pk[[k + 1, k]]
+        Mk_inv = np.eye(n, dtype=dt)
+        Mk_inv[k + 1, k] = Lm[k]
+        Minv = Minv @ Pk.T @ Mk_inv
+    return Minv, Ud  # H - lam I = Minv U
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_lu_real_solve_matches_exact_rational(n, seed):
+    H = random_hessenberg(n, seed)
+    b = hi.normal(seed, 51, n)
+    lam = float(hi.uniform(seed, 52, 1, -2.0, 2.0)[0])
+    x, e, U, Lm, piv, rep = oracle.lu_real(H, lam, b)
+    xe = exact_solve(H, lam, b).real
+    kappa = np.linalg.cond(H - lam * np.eye(n))
+    err = np.linalg.norm(x * 2.0 ** e - xe) / np.linalg.norm(xe)
+    assert err <= 4 * n * kappa * EPS, (err, kappa)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 12])
+def test_lu_complex_solve_matches_exact_rational(n):
+    H = random_hessenberg(n, 4)
+    b = hi.normal(4, 51, n) + 1j * hi.normal(4, 53, n)
+    lam = complex(hi.uniform(4, 52, 1, -2.0, 2.0)[0], hi.uniform(4, 54, 1, 0.1, 2.0)[0])
+    x, e, U, Lm, piv, rep = oracle.lu_cplx(H, lam, b)
+    xe = exact_solve(H, lam, b)
+    kappa = np.linalg.cond(H - lam * np.eye(n))
+    assert np.linalg.norm(x * 2.0 ** e - xe) / np.linalg.norm(xe) <= 4 * n * kappa * EPS
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_lu_factors_reproduce_the_shifted_matrix_with_bounded_multipliers(cplx):
+    # P (H - lambda I) = L U with |l_k| <= 1 (partial pivoting) and U upper
+    # triangular; a zero leading entry forces the first interchange
+    n = 33
+    H = random_hessenberg(n, 17)
+    lam = H[0, 0] + (0.5j if cplx else 0.0)
+    if cplx:
+        x, e, U, Lm, piv, rep = oracle.lu_cplx(H, lam, np.ones(n, dtype=complex))
+    else:
+        x, e, U, Lm, piv, rep = oracle.lu_real(H, lam, np.ones(n))
+    assert np.all(np.abs(Lm[:n - 1]) <= 1.0)
+    if not cplx:
+        assert piv[0] == 1  # h(0,0) - lambda = 0: the subdiagonal entry must pivot
+    Minv, Ud = _lu_factors(n, U, Lm, piv)
+    M = H - lam * np.eye(n)
+    assert np.abs(Minv @ Ud - M).max() <= 8 * n * EPS * np.abs(M).max()
+
+
+def test_lu_companion_eigenvectors_closed_form():
+    n = 6
+    roots = np.arange(1, n + 1, dtype=np.float64)
+    C = hi.companion(roots)
+    X, status = oracle.hsein_lu(C, roots, np.zeros(n), B=hi.unit_columns(n, n, seed=n))
+    assert np.all(status == 0)
+    # the roots are one apart: twice the first-order bound n eps ||C|| / gap
+    bound = 2 * n * EPS * np.abs(C).sum(axis=1).max()
+    for l, r in enumerate(roots):
+        assert angle(X[:, l], r ** np.arange(n - 1, -1, -1, dtype=np.float64)) <= bound
+
+
+def test_lu_scaling_is_needed_and_exact():
+    # back-substitution growth of 1e200 per row: the unprotected LU solve
+    # overflows, the protected one scales (the exponent carries the growth)
+    # and equals the exact solution's direction, real and complex
+    n = 6
+    H = np.eye(n) + 1e200 * np.triu(np.ones((n, n)), 1) + 1e-3 * np.diag(np.ones(n - 1), -1)
+    b = np.ones(n)
+    with np.errstate(all="ignore"):
+        x, e, U, Lm, piv, rep = oracle.lu_real(H, 0.5, b, robust=False)
+    assert not np.all(np.isfinite(x))
+    x, e, U, Lm, piv, rep = oracle.lu_real(H, 0.5, b)
+    assert e > 0 and np.all(np.isfinite(x))
+    assert angle(x / np.abs(x).max(), exact_solve(H, 0.5, b, direction=True).real) <= 1e-13
+    bc = b.astype(complex)
+    with np.errstate(all="ignore"):
+        xc, e, U, Lm, piv, rep = oracle.lu_cplx(H, 0.5 + 0.25j, bc, robust=False)
+    assert not np.all(np.isfinite(xc))
+    xc, e, U, Lm, piv, rep = oracle.lu_cplx(H, 0.5 + 0.25j, bc)
+    assert e > 0 and np.all(np.isfinite(xc))
+    assert angle(xc / np.abs(xc).max(), exact_solve(H, 0.5 + 0.25j, bc, direction=True)) <= 1e-13
+    # growth in the forward substitution: H - 0 I = L U with L unit lower
+    # bidiagonal (-1 below the diagonal, every multiplier -1) and U = I, so
+    # x = L^-1 b is the running sum of b; with b near the top of the double
+    # range the unprotected forward solve overflows, the protected one gives
+    # the closed-form direction (1, 2, ..., n) / ||.||
+    m = 9
+    H = np.eye(m) - np.diag(np.ones(m - 1), -1)
+    b = np.full(m, 1e308)
+    with np.errstate(all="ignore"):
+        x, e, U, Lm, piv, rep = oracle.lu_real(H, 0.0, b, robust=False)
+    assert not np.all(np.isfinite(x))
+    x, e, U, Lm, piv, rep = oracle.lu_real(H, 0.0, b)
+    assert e > 0 and np.all(np.isfinite(x)) and np.all(piv == 0)
+    assert angle(x, np.arange(1.0, m + 1)) <= 4 * m * EPS
+    # the bad system of Sec. 5.2 with a lowered threshold: scaling triggers
+    # at small n and the direction is exact
+    m = 40
+    H = hi.paper_h2(m)
+    x, e, U, Lm, piv, rep = oracle.lu_real(H, 2.0, np.ones(m), log2_omega=30.0)
+    assert e > 0 and np.all(np.isfinite(x))
+    assert angle(x, exact_solve(H, 2.0, np.ones(m)).real) <= 1e-13
+
+
+def test_lu_bad_system_h2_at_full_threshold():
+    # at n = 1024 the shift is an eigenvalue of H2 to working accuracy: the
+    # final pivot is replaced and the normalized result is an eigenvector
+    # (small normwise residual in long double)
+    n = 1024
+    H = hi.paper_h2(n)
+    X, status = oracle.hsein_lu(H, [2.0], [0.0], np.ones((n, 1)) / np.sqrt(n))
+    assert status[0] == 0 and np.all(np.isfinite(X))
+    y = X[:, 0].astype(np.longdouble)
+    M = H.astype(np.longdouble)
+    r = np.abs(M @ y - np.longdouble(2.0) * y).sum()
+    assert float(r / (np.abs(M).sum(axis=0).max() * np.abs(y).sum())) <= 100 * n * EPS
+
+
+def test_lu_driver_statuses_and_unit_norm():
+    inst = hi.small_instance(60, 4, 3, 9)
+    X, status = oracle.hsein_lu(inst.H, inst.wr, inst.wi, inst.B)
+    assert np.all(status == 0)
+    for lam, x in as_vectors(X, inst.wr, inst.wi):
+        assert abs(np.linalg.norm(x) - 1.0) <= 4 * inst.n * EPS
+        assert residual(inst.H, lam, x) <= 100 * inst.n * EPS
+    far = 1e3 * oracle.hnorm_inf(inst.H)
+    X, status = oracle.hsein_lu(inst.H, [far], [0.0], inst.B[:, :1])
+    assert status[0] == 1 and np.all(X == 0.0)
+
+
 # ---------------------------------------------------------------- restart
 # Alg. "hsrq3in" (Sec. 4.2): a new starting vector orthogonal to the previous
 # choices.  Pins: closed forms at n = 2 (real) and n = 3 (complex: the
