@@ -66,7 +66,7 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-requests", type=int, default=20000,
                     help="requests in the serving stream at 200 requests/s (the workload)")
-    ap.add_argument("--capacity-requests", type=int, default=4000,
+    ap.add_argument("--capacity-requests", type=int, default=2000,
                     help="requests per stream of the serving capacity sweep (0: skip)")
     ap.add_argument("--no-c2", action="store_true", help="skip the n = 8192 precision workload")
     ap.add_argument("--c2-steps", type=int, default=5)
@@ -222,7 +222,8 @@ def fp64_peak_tflops(sm_mhz, sms):
 
 def spawn_pool(workers, blas_threads):
     """A pool of spawned processes (safe beside an initialized CUDA context)
-    whose BLAS uses blas_threads threads."""
+    whose BLAS uses blas_threads threads, at a lower scheduling priority than
+    this process (which generates and measures the headline workload)."""
     import concurrent.futures as cf
     import multiprocessing as mp
     keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
@@ -230,7 +231,8 @@ def spawn_pool(workers, blas_threads):
     for k in keys:
         os.environ[k] = str(blas_threads)
     try:
-        ex = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+        ex = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"),
+                                    initializer=os.nice, initargs=(10,))
         ex.submit(int, 0).result()  # start the workers with these settings
     finally:
         for k, v in saved.items():
@@ -775,7 +777,7 @@ def main():
     # the GPU measures the headline workload
     bg, futs = None, {}
     if rank == 0 and world == 1 and (not args.no_c2 or not args.no_serve):
-        bg = spawn_pool(2, max(1, (os.cpu_count() or 2) // 3))
+        bg = spawn_pool(2, max(1, (os.cpu_count() or 2) // 2))
         if not args.no_c2:
             futs["c2"] = bg.submit(_gen_config2)
         if not args.no_serve:
