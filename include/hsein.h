@@ -72,11 +72,16 @@ typedef struct {
     int omega_log2; /* stored solution entries stay below 2^omega_log2; 0 = default (1000).  */
                     /* Lower values (>= 16) make the scaling of Sec. 4.1 trigger on small     */
                     /* problems, for testing                                                 */
-    int method;     /* 0 = the tiled level-3 solve (default); 1 = the comparison baseline:   */
-                    /*     Henry's RQ solve per shift, unblocked (Alg. "henry", the RQIN of   */
-                    /*     Sec. 5), one thread block per shift over the whole matrix, with   */
-                    /*     the same protection, normalization and backtransform; precision  */
-                    /*     must be 0                                                         */
+    int method;     /* 0 = the tiled level-3 solve (default); comparison baselines, one      */
+                    /*     thread block per shift over the whole matrix, with the same       */
+                    /*     protection, normalization and Varah test; precision must be 0:    */
+                    /*   1 = Henry's RQ solve per shift, unblocked (Alg. "henry", the RQIN   */
+                    /*     of Sec. 5), with the Givens backtransform;                        */
+                    /*   2 = the LU approach of LAPACK's inverse iteration (Sec. 2.1):       */
+                    /*     P (H - lambda I) = L U with partial pivoting, L y = P b,          */
+                    /*     U x = alpha y, for the given starting vector; the packed U of     */
+                    /*     every shift in flight is kept in the workspace (shifts are        */
+                    /*     factored in chunks that fit in 16 GiB); n <= 14336                */
     int givens;     /* storage of the Givens rotations between the solve and its            */
                     /*     backtransform: 0 = c and s as computed (default); 1 = compact     */
                     /*     (Sec. 4.4, Stewart's scheme): one number per real rotation, two   */
@@ -427,6 +432,15 @@ hsein_status hsein_server_progress(hsein_server_t server, long long *done, int m
 hsein_status hsein_server_stats(hsein_server_t server, int *pending, int *running,
                                 size_t *bytes_in_use, long long *requests_admitted,
                                 long long *solves_admitted);
+
+/*
+ * Head-of-line bypass: when the oldest pending request does not fit the
+ * arena, up to max_bypass later requests (looked for among the next 64) may
+ * be admitted ahead of it before admission waits for it again; each admitted
+ * request still takes its own footprint.  0 (the default) keeps strict
+ * arrival order.  The paper has no counterpart.
+ */
+hsein_status hsein_server_set_bypass(hsein_server_t server, int max_bypass);
 
 /* waits for the solves in flight, then frees everything */
 hsein_status hsein_server_destroy(hsein_server_t server);

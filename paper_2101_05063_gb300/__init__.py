@@ -14,8 +14,9 @@ is no CPU fallback: if the library cannot be loaded, every call raises.
     solver.solve_host(hH, hwr, hwi, hB, hQ0, hZ, hst) # the same from pinned host buffers
 
 Options of Solver: precision=1 (split-precision products on the BF16 tensor
-cores, the fast mode), givens=1 (compact rotation storage), method=1 (the
-per-shift baseline), br (tile height), robust, omega_log2.  Batch runs many
+cores, the fast mode), givens=1 (compact rotation storage), method=1 / 2 (the
+per-shift baselines: Henry's RQ solve / the LU approach), br (tile height),
+robust, omega_log2, wait_limit_cycles.  Batch runs many
 independent instances in one captured graph; Server admits requests by HBM
 footprint and fuses those on the same matrix; balance/unbalance prepare
 graded matrices for the split-precision mode.
@@ -34,7 +35,7 @@ __all__ = [
     "hsein_restart", "hsein_batch_plan", "hsein_batch_solve", "hsein_batch_autotune",
     "hsein_batch_info", "hsein_batch_destroy", "HseinInstance", "HseinBatchConfig", "Batch",
     "HseinRequest", "hsein_server_create", "hsein_server_submit", "hsein_server_progress",
-    "hsein_server_stats", "hsein_server_destroy", "Server", "hsein_balance", "hsein_unbalance",
+    "hsein_server_stats", "hsein_server_destroy", "hsein_server_set_bypass", "Server", "hsein_balance", "hsein_unbalance",
     "balance", "unbalance", "hsein_gehrd_workspace", "hsein_gehrd", "gehrd",
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
@@ -135,6 +136,8 @@ def load(build_if_missing=True):
     lib.hsein_gehrd_workspace.argtypes = [ip, ctypes.POINTER(sz)]
     lib.hsein_gehrd.restype = ctypes.c_int
     lib.hsein_gehrd.argtypes = [ip, dp, ip, dp, ip, dp, ip, vp, sz, vp]
+    lib.hsein_server_set_bypass.restype = ctypes.c_int
+    lib.hsein_server_set_bypass.argtypes = [vp, ctypes.c_int]
     lib.hsein_fp64_rate.restype = ctypes.c_int
     lib.hsein_fp64_rate.argtypes = [ctypes.c_longlong, dp, ctypes.c_longlong,
                                     ctypes.POINTER(ctypes.c_double), vp]
@@ -352,6 +355,10 @@ def hsein_server_stats(server):
                                      ctypes.byref(ra), ctypes.byref(sa)), "hsein_server_stats")
     return {"pending": p.value, "running": r.value, "bytes_in_use": b.value,
             "requests_admitted": ra.value, "solves_admitted": sa.value}
+
+
+def hsein_server_set_bypass(server, max_bypass):
+    return load().hsein_server_set_bypass(server, int(max_bypass))
 
 
 def hsein_server_destroy(server):
@@ -666,7 +673,7 @@ class Server:
     call; result(ticket) gives (X, status) of a completed request."""
 
     def __init__(self, hbm_bytes, max_jobs=8, max_merge_shifts=4096, robust=True,
-                 omega_log2=1000, device=None):
+                 omega_log2=1000, device=None, max_bypass=0):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -675,6 +682,8 @@ class Server:
         opt.omega_log2 = int(omega_log2)
         with torch.cuda.device(self.device):
             self.server = hsein_server_create(hbm_bytes, max_jobs, max_merge_shifts, opt)
+        if max_bypass:
+            _check(hsein_server_set_bypass(self.server, max_bypass), "hsein_server_set_bypass")
         self._live = {}
 
     def __del__(self):

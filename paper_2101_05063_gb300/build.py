@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libhsein.so")
 SOURCES = ["api.cu", "k_prep.cu", "k_diag.cu", "k_update.cu", "k_final.cu", "k_q0.cu",
            "k_ozaki_q0.cu", "k_update_oz.cu", "noalloc.cu", "tc_host.cu", "restart.cu", "batch.cu", "server.cu", "balance.cu", "k_henry.cu",
-           "gehrd.cu", "probe.cu"]
+           "gehrd.cu", "probe.cu", "k_lu.cu"]
 HEADERS = ["common.cuh", "ozaki.cuh", "tc.cuh"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 

@@ -50,7 +50,15 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-void make_layout(Layout* L, int n, int mr, int mc, int br, int precision, int givens) {
+// the LU baseline keeps the carried row (complex) in shared memory
+constexpr int kLuMaxN = 14336;
+
+// the per-shift LU baseline keeps the packed U factors of this many bytes at
+// most (the shifts are factored in chunks that fit)
+constexpr size_t kLuBudget = size_t(16) << 30;
+
+void make_layout(Layout* L, int n, int mr, int mc, int br, int precision, int givens,
+                 int method) {
     L->n = n;
     L->mr = mr;
     L->mc = mc;
@@ -101,6 +109,20 @@ void make_layout(Layout* L, int n, int mr, int mc, int br, int precision, int gi
     // which stays readable (hsein_plan_sync_status) after the backtransform
     L->off_oz = o;
     if (precision == 1) o = align256(o + hsein::ozq0_workspace_bytes(n, L->ncol));
+    // per-shift LU baseline: H row-major, and one slot (packed U, row maxima)
+    // per shift factored at once
+    L->lu_slots = 0;
+    L->lu_slot_bytes = 0;
+    L->off_hr = o;
+    L->off_lu = o;
+    if (method == 2) {
+        L->lu_slot_bytes = hsein::lu_slot_bytes(n);
+        const size_t fit = std::max<size_t>(1, kLuBudget / L->lu_slot_bytes);
+        L->lu_slots = (int)std::min<size_t>(fit, (size_t)std::max(mr, mc));
+        L->off_hr = take(sizeof(double) * nn * nn);
+        L->off_lu = take(L->lu_slot_bytes * (size_t)L->lu_slots);
+        o = align256(o);
+    }
     L->total = o;
 }
 
@@ -180,8 +202,9 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         if (opt->wait_limit_cycles != 0) o.wait_limit_cycles = opt->wait_limit_cycles;
     }
     if (o.wait_limit_cycles < 1 || o.wait_limit_cycles > (1LL << 60)) return HSEIN_EARG;
-    if (o.method != 0 && o.method != 1) return HSEIN_EARG;
-    if (o.method == 1 && o.precision != 0) return HSEIN_EARG;  // the baseline is FP64
+    if (o.method < 0 || o.method > 2) return HSEIN_EARG;
+    if (o.method != 0 && o.precision != 0) return HSEIN_EARG;  // the baselines are FP64
+    if (o.method == 2 && n > kLuMaxN) return HSEIN_EARG;       // its row w in shared memory
     if (o.givens != 0 && o.givens != 1) return HSEIN_EARG;
     if (o.givens == 1 && o.method != 0) return HSEIN_EARG;  // the baseline stores c and s
     if (o.br < 8 || o.br > hsein::kMaxBr || o.br % 8 != 0) return HSEIN_EARG;
@@ -191,12 +214,13 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
     if (o.omega_log2 < 16 || o.omega_log2 > 1000) return HSEIN_EARG;
     hsein_plan_s* p = new (std::nothrow) hsein_plan_s;
     if (!p) return HSEIN_ENOMEM;
-    make_layout(&p->L, n, m_real, m_cplx, o.br, o.precision, o.givens);
+    make_layout(&p->L, n, m_real, m_cplx, o.br, o.precision, o.givens, o.method);
     p->opt = o;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
         hsein::diag_configure(o.br) != cudaSuccess || hsein::update_configure(o.br) != cudaSuccess ||
-        hsein::ozaki_configure() != cudaSuccess || hsein::update_oz_configure() != cudaSuccess) {
+        hsein::ozaki_configure() != cudaSuccess || hsein::update_oz_configure() != cudaSuccess ||
+        (o.method == 2 && hsein::lu_configure(n) != cudaSuccess)) {
         cudaGetLastError();
         delete p;
         return HSEIN_ECUDA;
@@ -239,15 +263,17 @@ hsein_status hsein_solve(hsein_plan_t plan, const double* dH, int ldh, const dou
         }
         plan->maps_work = dWork;
     }
-    if (plan->opt.method == 1) {
-        // comparison baseline: Henry's solve per shift over the whole matrix
+    if (plan->opt.method != 0) {
+        // comparison baselines, per shift over the whole matrix: Henry's RQ
+        // solve (1) or the LU approach (2)
         {
             PhaseScope ps(plan, 0, s);
             hsein::launch_prepare(L, dWork, dH, ldh, dWr, dWi, dB, ldb, om, s);
         }
         {
             PhaseScope ps(plan, 1, s);
-            hsein::launch_henry(L, dWork, dH, ldh, robust, om, s);
+            if (plan->opt.method == 1) hsein::launch_henry(L, dWork, dH, ldh, robust, om, s);
+            else hsein::launch_lu(L, dWork, dH, ldh, robust, om, s);
         }
         {
             PhaseScope ps(plan, 3, s);

@@ -62,9 +62,11 @@ struct Layout {
     int n, m, mr, mc, ncol, ncolp, br, N, b0, ldw;
     size_t off_state, off_qsrc, off_qcol, off_lam, off_bnorm, off_eB, off_etile, off_bmax,
         off_rmax, off_epi, off_anorm, off_rowpart, off_X, off_R, off_Cr, off_Ci, off_S, off_ZW,
-        off_dt, off_hd, off_he, off_zwd, off_zwf, off_margin, off_oz, total;
+        off_dt, off_hd, off_he, off_zwd, off_zwf, off_margin, off_oz, off_hr, off_lu, total;
     int oz;       // 1: split-precision shared-H update (BF16 digits), 0: FP64
     int compact;  // 1: Givens rotations stored compactly (Stewart's scheme)
+    int lu_slots;          // per-shift LU baseline: shifts factored at once
+    size_t lu_slot_bytes;  // and the workspace of one (packed U, row maxima)
 };
 
 // first row of tile J (tile 0 is the ragged top-left tile of height b0)
@@ -231,6 +233,11 @@ void launch_prepare(const Layout& L, void* work, const double* H, int ldh, const
 void launch_diag(const Layout& L, void* work, int J, int robust, int omega_log2,
                  long long wait_limit, cudaStream_t s);
 void launch_update(const Layout& L, void* work, const double* H, int ldh, int J, cudaStream_t s);
+// per-shift LU comparison baseline (method 2)
+size_t lu_slot_bytes(int n);
+void launch_lu(const Layout& L, void* work, const double* H, int ldh, int robust, int omega_log2,
+               cudaStream_t s);
+cudaError_t lu_configure(int n);
 // split-precision update: tensor maps of the A_J digit blocks (mapsA[1..N-1])
 // and of the [Z'|W] digits for the workspace at `work`
 bool encode_update_oz_maps(const Layout& L, void* work, CUtensorMap* mapsA, CUtensorMap* mapB);

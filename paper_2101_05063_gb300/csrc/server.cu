@@ -131,6 +131,11 @@ struct hsein_server_s {
     std::deque<long long> finished;
     long long next_ticket = 1;
     long long req_admitted = 0, solves_admitted = 0;
+    // head-of-line bypass: later requests admitted while the oldest one does
+    // not fit, at most max_bypass of them per oldest request
+    int max_bypass = 0;
+    long long head_ticket = 0;
+    int head_bypassed = 0;
 };
 
 namespace {
@@ -250,6 +255,58 @@ hsein_status retire(hsein_server_s* S) {
     return HSEIN_OK;
 }
 
+// admit pending request h (and the later pending requests that can share its
+// solve) into `slot` if its footprint fits the arena; *done tells whether it
+// did
+hsein_status try_admit(hsein_server_s* S, size_t h, int slot, bool* done) {
+    *done = false;
+    std::vector<size_t> group{h};
+    int M = shifts(S->pending[h].req);
+    for (size_t i = h + 1; i < S->pending.size(); ++i) {
+        const hsein_request& r = S->pending[i].req;
+        if (same_solve(r, S->pending[h].req) && M + shifts(r) <= S->max_merge) {
+            group.push_back(i);
+            M += shifts(r);
+        }
+    }
+    // the largest prefix of the group whose footprint fits the arena now
+    hsein_plan_t plan = nullptr;
+    size_t ws = 0, total = 0, off = kNoBlock;
+    for (;;) {
+        const hsein_status rc = footprint(S, group, &plan, &ws, &total);
+        if (rc != HSEIN_OK) return rc;
+        off = S->arena.alloc(total);
+        if (off != kNoBlock) break;
+        hsein_plan_destroy(plan);
+        plan = nullptr;
+        if (group.size() == 1) return HSEIN_OK;  // does not fit now
+        group.pop_back();
+    }
+    Job job;
+    job.plan = plan;
+    job.off = off;
+    job.bytes = total;
+    job.slot = slot;
+    for (size_t i : group) job.tickets.push_back(S->pending[i].ticket);
+    const hsein_status rc = launch(S, group, plan, ws, off, total, slot);
+    if (rc != HSEIN_OK) {
+        S->arena.free(off, total);
+        hsein_plan_destroy(plan);
+        return rc;
+    }
+    S->busy[slot] = true;
+    S->running.push_back(job);
+    S->req_admitted += (long long)group.size();
+    S->solves_admitted += 1;
+    for (auto it = group.rbegin(); it != group.rend(); ++it)
+        S->pending.erase(S->pending.begin() + (std::ptrdiff_t)*it);
+    *done = true;
+    return HSEIN_OK;
+}
+
+// how many pending requests behind the oldest one are looked at for a bypass
+constexpr size_t kBypassScan = 64;
+
 hsein_status admit(hsein_server_s* S) {
     while (!S->pending.empty()) {
         int slot = -1;
@@ -260,46 +317,25 @@ hsein_status admit(hsein_server_s* S) {
             }
         if (slot < 0) return HSEIN_OK;
         // the oldest request and the later ones that can share its solve
-        std::vector<size_t> group{0};
-        int M = shifts(S->pending[0].req);
-        for (size_t i = 1; i < S->pending.size(); ++i) {
-            const hsein_request& r = S->pending[i].req;
-            if (same_solve(r, S->pending[0].req) && M + shifts(r) <= S->max_merge) {
-                group.push_back(i);
-                M += shifts(r);
-            }
+        const long long head = S->pending[0].ticket;
+        bool done = false;
+        hsein_status rc = try_admit(S, 0, slot, &done);
+        if (rc != HSEIN_OK) return rc;
+        if (done) continue;
+        // it does not fit: wait for memory (arrival order is kept), unless
+        // later requests may bypass it
+        if (S->head_ticket != head) {
+            S->head_ticket = head;
+            S->head_bypassed = 0;
         }
-        // the largest prefix of the group whose footprint fits the arena now
-        hsein_plan_t plan = nullptr;
-        size_t ws = 0, total = 0, off = kNoBlock;
-        for (;;) {
-            const hsein_status rc = footprint(S, group, &plan, &ws, &total);
+        if (S->head_bypassed >= S->max_bypass) return HSEIN_OK;
+        const size_t lim = std::min(S->pending.size(), kBypassScan + 1);
+        for (size_t h = 1; h < lim && !done; ++h) {
+            rc = try_admit(S, h, slot, &done);
             if (rc != HSEIN_OK) return rc;
-            off = S->arena.alloc(total);
-            if (off != kNoBlock) break;
-            hsein_plan_destroy(plan);
-            plan = nullptr;
-            if (group.size() == 1) return HSEIN_OK;  // wait for memory (arrival order is kept)
-            group.pop_back();
         }
-        Job job;
-        job.plan = plan;
-        job.off = off;
-        job.bytes = total;
-        job.slot = slot;
-        for (size_t i : group) job.tickets.push_back(S->pending[i].ticket);
-        const hsein_status rc = launch(S, group, plan, ws, off, total, slot);
-        if (rc != HSEIN_OK) {
-            S->arena.free(off, total);
-            hsein_plan_destroy(plan);
-            return rc;
-        }
-        S->busy[slot] = true;
-        S->running.push_back(job);
-        S->req_admitted += (long long)group.size();
-        S->solves_admitted += 1;
-        for (auto it = group.rbegin(); it != group.rend(); ++it)
-            S->pending.erase(S->pending.begin() + (std::ptrdiff_t)*it);
+        if (!done) return HSEIN_OK;
+        S->head_bypassed += 1;
     }
     return HSEIN_OK;
 }
@@ -320,6 +356,12 @@ void destroy(hsein_server_s* S) {
 }  // namespace
 
 extern "C" {
+
+hsein_status hsein_server_set_bypass(hsein_server_t server, int max_bypass) {
+    if (!server || max_bypass < 0) return HSEIN_EARG;
+    server->max_bypass = max_bypass;
+    return HSEIN_OK;
+}
 
 hsein_status hsein_server_create(hsein_server_t* server, size_t hbm_bytes, int max_jobs,
                                  int max_merge_shifts, const hsein_options* opt) {

@@ -102,6 +102,41 @@ def test_admission_waits_for_memory(pool):
         assert np.array_equal(s.cpu().numpy(), sa) and np.array_equal(X.cpu().numpy(), Xa)
 
 
+@pytest.mark.parametrize("bypass", [0, 4])
+def test_head_of_line_bypass(pool, bypass):
+    # an arena for one n = 1024 solve and one n = 256 solve: behind a large
+    # request that must wait for memory, a small one waits too in arrival
+    # order (bypass 0), or is admitted ahead of it (bypass > 0); every result
+    # equals the request's solve alone
+    p, dev = pool
+    big_r = [r for r in _requests(p, 40, 15) if r["n"] == 1024][:2]
+    small_r = [r for r in _requests(p, 40, 16) if r["n"] == 256][:1]
+    opt = hs.hsein_default_options()
+    opt.precision = 1
+
+    def ws(r):
+        mc = int((r["wi"] != 0).sum())
+        plan, w = hs.hsein_plan(r["n"], len(r["wr"]) - mc, mc, opt)
+        hs.hsein_plan_destroy(plan)
+        return w
+    wb = max(ws(r) for r in big_r)
+    arena = wb + ws(small_r[0]) + (1 << 20)
+    assert arena < 2 * min(ws(r) for r in big_r)
+    srv = hs.Server(arena, max_jobs=4, max_merge_shifts=1, max_bypass=bypass)
+    order = big_r + small_r
+    tickets = [srv.submit(dev[r["n"]][r["index"]][0], to_dev(r["wr"]), to_dev(r["wi"]),
+                          precision=1) for r in order]
+    done = set(srv.progress())  # admission happens here
+    st = srv.stats()
+    assert st["running"] + len(done) == (2 if bypass else 1)
+    while len(done) < len(tickets):
+        done |= set(srv.progress(wait=True))
+    for r, t in zip(order, tickets):
+        X, s = srv.result(t)
+        Xa, sa = _alone(dev[r["n"]][r["index"]][0], to_dev(r["wr"]), to_dev(r["wi"]), 1)
+        assert np.array_equal(s.cpu().numpy(), sa) and np.array_equal(X.cpu().numpy(), Xa)
+
+
 def test_oversized_request_is_refused(pool):
     p, dev = pool
     srv = hs.Server(1 << 20, max_jobs=2, max_merge_shifts=64)
