@@ -531,11 +531,12 @@ def measure_serving(args, torch, hs, hi, pool, t_gen):
     replay_stream(srv, pool_dev, wl, torch, keep=False)
     replay_stream(srv, pool_dev, wl, torch, keep=False, precision=0)
 
-    def run(count, rate, precision, seed=4):
+    def run(count, rate, precision, seed=4, server=None):
+        srv_ = server or srv
         reqs = hi.serving_requests(pool, count, seed=seed, rate=rate)
-        s0 = srv.stats()
-        times, status = replay_stream(srv, pool_dev, reqs, torch, keep=False, precision=precision)
-        s1 = srv.stats()
+        s0 = srv_.stats()
+        times, status = replay_stream(srv_, pool_dev, reqs, torch, keep=False, precision=precision)
+        s1 = srv_.stats()
         lat = np.array([c - a for a, c in times]) * 1e3
         conv = sum(int(sum(2 if w != 0 else 1 for w, st in zip(r["wi"], status[j]) if st == 0))
                    for j, r in enumerate(reqs))
@@ -570,6 +571,11 @@ def measure_serving(args, torch, hs, hi, pool, t_gen):
     if args.capacity_requests > 0:
         cap = [run(args.capacity_requests, 200.0 * k, 1, seed=50 + k) for k in (2, 4, 8)]
         cap.append(run(args.capacity_requests, 1600.0, 0, seed=58))
+        # the 2x stream again with head-of-line bypass (up to 8 later requests
+        # may pass one that does not fit the arena)
+        srv_b = hs.Server(64 << 30, max_jobs=8, max_merge_shifts=4096, max_bypass=8)
+        byp = run(args.capacity_requests, 400.0, 1, seed=52, server=srv_b)
+        del srv_b
         sat = [c for c in cap if c["span_s"] > 1.2 * c["arrival_span_s"]]
         out["capacity"] = {
             "streams": cap,
@@ -578,6 +584,9 @@ def measure_serving(args, torch, hs, hi, pool, t_gen):
             "saturated_fp64_value": cap[-1]["value"],
             "split_over_fp64": cap[2]["value"] / cap[-1]["value"] if cap[-1]["value"] else None,
             "saturated_streams": [(c["rate_per_s"], c["precision"]) for c in sat],
+            "bypass_2x": {"p50": byp["latency"]["p50"], "p99": byp["latency"]["p99"],
+                          "value": byp["value"], "without_bypass_p99": cap[0]["latency"]["p99"],
+                          "how": "the same 2x stream with hsein_server_set_bypass(8)"},
             "how": "%d-request streams at 2x, 4x, 8x the rate (split products) and at 8x with "
                    "FP64 products; a stream whose completion span exceeds its arrival span is "
                    "saturated, and its eigvecs/s is the service's capacity"
@@ -949,6 +958,18 @@ def main():
                 "not_converged": int((sh_b != 0).sum()),
                 "phases": {k: {"ms_per_step": v[0] / bsteps} for k, v in prof_b.items()}}
 
+    # the other comparison baseline: the LU approach per shift (Sec. 2.1,
+    # LAPACK's inverse iteration), FP64, same workload and backtransform
+    log("per-shift LU baseline")
+    _, _, ms_l, prof_l, worst_l, sh_l, _, lat_l = measure(0, False, method=2, steps=bsteps)
+    lu_baseline = {"method": "LU with partial pivoting per shift (P (H - lambda I) = L U, "
+                             "L y = P b, U x = alpha y; one thread block per shift, U kept "
+                             "packed in HBM), FP64; same prepare, normalization and z = Q0 x",
+                   "value": sum_over_ranks(converged_columns(sh_l), world) * bsteps / (ms_l * 1e-3),
+                   "unit": UNIT, "ms_per_step": ms_l / bsteps, "residual_max_over_n_eps": worst_l,
+                   "not_converged": int((sh_l != 0).sum()),
+                   "phases": {k: {"ms_per_step": v[0] / bsteps} for k, v in prof_l.items()}}
+
     if rank != 0:
         return
     pk, pk_kind = peaks()
@@ -1058,6 +1079,7 @@ def main():
         "restart": restart,
         "plain_fp64": plain,
         "per_shift_baseline": baseline,
+        "per_shift_lu_baseline": lu_baseline,
         "compact_givens": compact,
     }
     if not args.no_reduction and world == 1:
