@@ -66,7 +66,7 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-requests", type=int, default=20000,
                     help="requests in the serving stream at 200 requests/s (the workload)")
-    ap.add_argument("--capacity-requests", type=int, default=2000,
+    ap.add_argument("--capacity-requests", type=int, default=1500,
                     help="requests per stream of the serving capacity sweep (0: skip)")
     ap.add_argument("--no-c2", action="store_true", help="skip the n = 8192 precision workload")
     ap.add_argument("--c2-steps", type=int, default=5)
@@ -786,7 +786,9 @@ def main():
     # the GPU measures the headline workload
     bg, futs = None, {}
     if rank == 0 and world == 1 and (not args.no_c2 or not args.no_serve):
-        bg = spawn_pool(2, max(1, (os.cpu_count() or 2) // 2))
+        # one worker, the n = 8192 workload first (it is needed first), all
+        # cores for its BLAS
+        bg = spawn_pool(1, os.cpu_count() or 1)
         if not args.no_c2:
             futs["c2"] = bg.submit(_gen_config2)
         if not args.no_serve:
