@@ -878,8 +878,9 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
-    # the binding's end-to-end call: inputs up, solve (Q0's upload overlapped
-    # with it), backtransform, Z and the status codes down
+    # the C ABI's end-to-end call (hsein_solve_host): inputs up, solve (Q0's
+    # upload overlapped with it on the plan's side stream), backtransform, Z
+    # and the status codes down
     def time_e2e(slv):
         slv.solve_host(hH, hwr, hwi, hB, hQ, hZ, hS)
         torch.cuda.synchronize()

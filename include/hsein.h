@@ -175,6 +175,28 @@ hsein_status hsein_backtransform(hsein_plan_t plan, const double *dQ0, int ldq,
                                  void *dWork, size_t work_bytes, void *stream);
 
 /*
+ * The solve and z = Q0 x from host memory, end to end (Sec. 1: eigenvectors
+ * of A = Q0 H Q0^T): H, the shifts and B are copied to the device on
+ * `stream`; Q0 on a side stream owned by the plan meanwhile (only the
+ * backtransform needs it; it waits for the previous call's backtransform to
+ * have read the device copy); then hsein_solve, hsein_backtransform, and Z
+ * and the statuses are copied back.  Host arrays: hH n x n (ldh >= n), hWr,
+ * hWi m shifts, hB n x ncol (ldb >= n) or NULL for rho*e, hQ0 n x n
+ * (ldq >= n), hZ n x ncol output (ldz >= n), hStatus m output; pinned host
+ * memory lets the copies run asynchronously.  dWork: device memory of
+ * hsein_host_workspace bytes (the solve's workspace followed by the device
+ * copies of the operands), 256-byte aligned.  Stream-ordered: hZ and
+ * hStatus are valid once `stream` has completed.  Device errors as for
+ * hsein_solve (hsein_plan_sync_status on dWork).  The paper has no
+ * counterpart: an interface convenience.
+ */
+hsein_status hsein_host_workspace(hsein_plan_t plan, size_t *workspace_bytes);
+hsein_status hsein_solve_host(hsein_plan_t plan, const double *hH, int ldh,
+                              const double *hWr, const double *hWi, const double *hB, int ldb,
+                              const double *hQ0, int ldq, double *hZ, int ldz, int *hStatus,
+                              void *dWork, size_t work_bytes, void *stream);
+
+/*
  * Restart loop of inverse iteration (Alg. "hsrq3in", Sec. 4.2).  Call after
  * hsein_solve with the same arguments: every shift whose status is
  * HSEIN_COL_NOT_CONVERGED is solved again, up to max_tries times, from a new

@@ -39,7 +39,8 @@ __all__ = [
     "balance", "unbalance", "hsein_gehrd_workspace", "hsein_gehrd", "gehrd",
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
-    "STATUS", "PHASES", "hsein_fp64_rate", "fp64_rate",
+    "STATUS", "PHASES", "hsein_fp64_rate", "fp64_rate", "hsein_host_workspace",
+    "hsein_solve_host",
 ]
 
 STATUS = {0: "HSEIN_OK", -1: "HSEIN_EARG", -2: "HSEIN_ENOMEM", -3: "HSEIN_ENOTUNREDUCED",
@@ -136,6 +137,10 @@ def load(build_if_missing=True):
     lib.hsein_gehrd_workspace.argtypes = [ip, ctypes.POINTER(sz)]
     lib.hsein_gehrd.restype = ctypes.c_int
     lib.hsein_gehrd.argtypes = [ip, dp, ip, dp, ip, dp, ip, vp, sz, vp]
+    lib.hsein_host_workspace.restype = ctypes.c_int
+    lib.hsein_host_workspace.argtypes = [vp, ctypes.POINTER(sz)]
+    lib.hsein_solve_host.restype = ctypes.c_int
+    lib.hsein_solve_host.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, ip, dp, vp, sz, vp]
     lib.hsein_server_set_bypass.restype = ctypes.c_int
     lib.hsein_server_set_bypass.argtypes = [vp, ctypes.c_int]
     lib.hsein_fp64_rate.restype = ctypes.c_int
@@ -365,6 +370,19 @@ def hsein_server_destroy(server):
     return load().hsein_server_destroy(server)
 
 
+def hsein_host_workspace(plan):
+    """Device bytes hsein_solve_host needs."""
+    w = ctypes.c_size_t()
+    _check(load().hsein_host_workspace(plan, ctypes.byref(w)), "hsein_host_workspace")
+    return w.value
+
+
+def hsein_solve_host(plan, hH, ldh, hWr, hWi, hB, ldb, hQ0, ldq, hZ, ldz, hStatus, dWork,
+                     work_bytes, stream):
+    return load().hsein_solve_host(plan, hH, ldh, hWr, hWi, hB, ldb, hQ0, ldq, hZ, ldz,
+                                   hStatus, dWork, work_bytes, stream)
+
+
 def hsein_fp64_rate(iters, dOut, count, stream):
     """Launch the FP64 rate probe; returns its flop count."""
     f = ctypes.c_double()
@@ -545,43 +563,32 @@ class Solver:
         return out
 
     def solve_host(self, hH, hwr, hwi, hB, hQ0, hZ, hstatus):
-        """End to end from host memory: H, the shifts and B go to the device
-        first; Q0 follows on a second stream while the solve runs (it is
-        needed only by the backtransform); Z = Q0 X and the status codes come
-        back into hZ and hstatus.  Host tensors should be pinned and laid out
-        like the device operands (column-major).  Stream-ordered on the
-        current stream: synchronize before reading hZ and hstatus.  Device
-        buffers are allocated on the first call and reused."""
+        """End to end from host memory through hsein_solve_host: H, the shifts
+        and B go to the device first; Q0 follows on the plan's side stream
+        while the solve runs (it is needed only by the backtransform); Z = Q0 X
+        and the status codes come back into hZ and hstatus.  Host tensors
+        should be pinned and laid out like the device operands (column-major).
+        Stream-ordered on the current stream: synchronize before reading hZ
+        and hstatus.  The device workspace is allocated on the first call and
+        reused."""
         torch = self.torch
-        st = torch.cuda.current_stream(self.device)
-        if getattr(self, "_e2e", None) is None:
-            mk = lambda r, c: torch.empty((c, r), dtype=torch.float64, device=self.device).t()
-            self._e2e = {"H": mk(self.n, self.n), "Q": mk(self.n, self.n),
-                         "B": mk(self.n, self.ncol), "X": mk(self.n, self.ncol),
-                         "Z": mk(self.n, self.ncol),
-                         "wr": torch.empty(self.m, dtype=torch.float64, device=self.device),
-                         "wi": torch.empty(self.m, dtype=torch.float64, device=self.device),
-                         "status": torch.empty(self.m, dtype=torch.int32, device=self.device),
-                         "side": torch.cuda.Stream(self.device)}
-        d = self._e2e
-        d["H"].copy_(hH, non_blocking=True)
-        d["wr"].copy_(hwr, non_blocking=True)
-        d["wi"].copy_(hwi, non_blocking=True)
-        if hB is not None:
-            d["B"].copy_(hB, non_blocking=True)
-        # Q0 after the solve's own inputs (they share the link) and after the
-        # previous call's backtransform has read the buffer
-        side = d["side"]
-        side.wait_stream(st)
-        with torch.cuda.stream(side):
-            d["Q"].copy_(hQ0, non_blocking=True)
-        X, status = self.solve(d["H"], d["wr"], d["wi"], d["B"] if hB is not None else None,
-                               X=d["X"], status=d["status"], check=False)
-        st.wait_stream(side)
-        Z = self.backtransform(d["Q"], X, d["Z"])
-        hZ.copy_(Z, non_blocking=True)
-        hstatus.copy_(status, non_blocking=True)
+        if getattr(self, "_hwork", None) is None:
+            nb = hsein_host_workspace(self.plan)
+            self._hwork = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        hH = _colmajor(hH, torch)
+        hQ0 = _colmajor(hQ0, torch)
+        hB = _colmajor(hB, torch) if hB is not None else None
+        rc = hsein_solve_host(self.plan, hH.data_ptr(), _ld(hH), hwr.data_ptr(), hwi.data_ptr(),
+                              hB.data_ptr() if hB is not None else 0,
+                              _ld(hB) if hB is not None else self.n, hQ0.data_ptr(), _ld(hQ0),
+                              hZ.data_ptr(), _ld(hZ), hstatus.data_ptr(), self._hwork.data_ptr(),
+                              self._hwork.numel(), self._stream())
+        _check(rc, "hsein_solve_host")
         return hZ, hstatus
+
+    def host_device_status(self):
+        """Device status of the last hsein_solve_host call."""
+        return hsein_plan_sync_status(self.plan, self._hwork.data_ptr(), self._stream())
 
     def backtransform(self, Q0, X, Z=None):
         """Z = Q0 X (eigenvectors of A = Q0 H Q0^T)."""

@@ -44,6 +44,10 @@ struct hsein_plan_s {
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     std::vector<int> rec_phase;
+    // hsein_solve_host: a side stream for the upload of Q0, and events that
+    // order it after the previous call's backtransform and before this one's
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_q0 = nullptr, ev_done = nullptr;
 };
 
 namespace {
@@ -455,6 +459,100 @@ hsein_status hsein_restart(hsein_plan_t plan, const double* dH, int ldh, const d
     return failed.empty() ? HSEIN_OK : HSEIN_WNOTCONVERGED;
 }
 
+// the device copies of hsein_solve_host's operands, after the solve's own
+// workspace: H and Q0 (n x n), B, X and Z (n x ncol, leading dimension n),
+// the shifts and the statuses
+namespace {
+struct HostLayout {
+    size_t off_h, off_q, off_b, off_x, off_z, off_wr, off_wi, off_st, total;
+};
+HostLayout host_layout(const Layout& L) {
+    HostLayout h;
+    size_t o = align256(L.total);
+    auto take = [&](size_t b) {
+        size_t at = o;
+        o = align256(o + b);
+        return at;
+    };
+    const size_t n = L.n, nc = L.ncol, m = L.m;
+    h.off_h = take(sizeof(double) * n * n);
+    h.off_q = take(sizeof(double) * n * n);
+    h.off_b = take(sizeof(double) * n * nc);
+    h.off_x = take(sizeof(double) * n * nc);
+    h.off_z = take(sizeof(double) * n * nc);
+    h.off_wr = take(sizeof(double) * m);
+    h.off_wi = take(sizeof(double) * m);
+    h.off_st = take(sizeof(int) * m);
+    h.total = o;
+    return h;
+}
+}  // namespace
+
+hsein_status hsein_host_workspace(hsein_plan_t plan, size_t* workspace_bytes) {
+    if (!plan || !workspace_bytes) return HSEIN_EARG;
+    *workspace_bytes = host_layout(plan->L).total;
+    return HSEIN_OK;
+}
+
+hsein_status hsein_solve_host(hsein_plan_t plan, const double* hH, int ldh, const double* hWr,
+                              const double* hWi, const double* hB, int ldb, const double* hQ0,
+                              int ldq, double* hZ, int ldz, int* hStatus, void* dWork,
+                              size_t work_bytes, void* stream) {
+    if (!plan) return HSEIN_EARG;
+    const Layout& L = plan->L;
+    if (!hH || ldh < L.n || !hWr || !hWi || !hQ0 || ldq < L.n || !hZ || ldz < L.n || !hStatus)
+        return HSEIN_EARG;
+    if (hB && ldb < L.n) return HSEIN_EARG;
+    if (!dWork || !aligned256(dWork)) return HSEIN_EARG;
+    const HostLayout h = host_layout(L);
+    if (work_bytes < h.total) return HSEIN_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!plan->side) {
+        if (cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&plan->ev_q0, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&plan->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return HSEIN_ECUDA;
+        }
+    }
+    char* w = static_cast<char*>(dWork);
+    double* dH = reinterpret_cast<double*>(w + h.off_h);
+    double* dQ = reinterpret_cast<double*>(w + h.off_q);
+    double* dB = reinterpret_cast<double*>(w + h.off_b);
+    double* dX = reinterpret_cast<double*>(w + h.off_x);
+    double* dZ = reinterpret_cast<double*>(w + h.off_z);
+    double* dWr = reinterpret_cast<double*>(w + h.off_wr);
+    double* dWi = reinterpret_cast<double*>(w + h.off_wi);
+    int* dSt = reinterpret_cast<int*>(w + h.off_st);
+    const size_t n = L.n, nc = L.ncol, m = L.m, row = sizeof(double) * n;
+    // the solve's inputs on the caller's stream; Q0 (needed only by the
+    // backtransform) on the side stream meanwhile, once the previous call's
+    // backtransform has read the device copy
+    bool ok = cudaMemcpy2DAsync(dH, row, hH, sizeof(double) * ldh, row, n, cudaMemcpyHostToDevice,
+                                s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dWr, hWr, sizeof(double) * m, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dWi, hWi, sizeof(double) * m, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (hB)
+        ok = ok && cudaMemcpy2DAsync(dB, row, hB, sizeof(double) * ldb, row, nc,
+                                     cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(plan->side, plan->ev_done, 0) == cudaSuccess;
+    ok = ok && cudaMemcpy2DAsync(dQ, row, hQ0, sizeof(double) * ldq, row, n,
+                                 cudaMemcpyHostToDevice, plan->side) == cudaSuccess;
+    ok = ok && cudaEventRecord(plan->ev_q0, plan->side) == cudaSuccess;
+    if (!ok) return HSEIN_ECUDA;
+    hsein_status rc = hsein_solve(plan, dH, (int)n, dWr, dWi, hB ? dB : nullptr, (int)n, dX,
+                                  (int)n, dSt, dWork, L.total, stream);
+    if (rc != HSEIN_OK) return rc;
+    if (cudaStreamWaitEvent(s, plan->ev_q0, 0) != cudaSuccess) return HSEIN_ECUDA;
+    rc = hsein_backtransform(plan, dQ, (int)n, dX, (int)n, dZ, (int)n, dWork, L.total, stream);
+    if (rc != HSEIN_OK) return rc;
+    ok = cudaEventRecord(plan->ev_done, s) == cudaSuccess;
+    ok = ok && cudaMemcpy2DAsync(hZ, sizeof(double) * ldz, dZ, row, row, nc,
+                                 cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(hStatus, dSt, sizeof(int) * m, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    return ok ? HSEIN_OK : HSEIN_ECUDA;
+}
+
 hsein_status hsein_margins(hsein_plan_t plan, const void* dWork, double* dMargin, void* stream) {
     if (!plan || !dWork || !dMargin) return HSEIN_EARG;
     const char* src = static_cast<const char*>(dWork) + plan->L.off_margin;
@@ -513,6 +611,9 @@ hsein_status hsein_plan_profile(hsein_plan_t plan, double* ms, int* launches, in
 hsein_status hsein_plan_destroy(hsein_plan_t plan) {
     if (plan) {
         for (cudaEvent_t e : plan->pool) cudaEventDestroy(e);
+        if (plan->ev_q0) cudaEventDestroy(plan->ev_q0);
+        if (plan->ev_done) cudaEventDestroy(plan->ev_done);
+        if (plan->side) cudaStreamDestroy(plan->side);
     }
     delete plan;
     return HSEIN_OK;

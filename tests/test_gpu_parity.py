@@ -367,8 +367,9 @@ def test_split_precision_bad_system_h2(n, om):
 
 
 def test_solve_host_matches_device_path():
-    # the end-to-end call from pinned host buffers gives the device path's
-    # results bit for bit (same kernels on the same inputs), twice in a row
+    # the end-to-end call from host buffers (hsein_solve_host) gives the
+    # device path's results bit for bit (same kernels on the same inputs),
+    # twice in a row from pinned memory, then from pageable memory
     inst = hi.small_instance(300, 9, 5, 44)
     n, ncol, m = inst.n, inst.ncol, inst.m
     s = hs.Solver(n, inst.m_real, inst.m_cplx)
@@ -384,6 +385,17 @@ def test_solve_host_matches_device_path():
         torch.cuda.synchronize()
         assert np.array_equal(hZ.numpy(), Z)
         assert np.array_equal(hS.numpy(), st)
+    # pageable host memory and the default starting vector: the same results
+    # as the device path with B = NULL
+    X0, st0 = s.solve(to_dev(inst.H), to_dev(inst.wr), to_dev(inst.wi), None)
+    Z0 = s.backtransform(to_dev(inst.Q0), X0).cpu().numpy()
+    hZ2 = torch.zeros((ncol, n), dtype=torch.float64).t()
+    hS2 = torch.zeros(m, dtype=torch.int32)
+    cm = lambda a: torch.as_tensor(np.asfortranarray(a), dtype=torch.float64)
+    s.solve_host(cm(inst.H), cm(inst.wr), cm(inst.wi), None, cm(inst.Q0), hZ2, hS2)
+    torch.cuda.synchronize()
+    assert np.array_equal(hZ2.numpy(), Z0) and np.array_equal(hS2.numpy(), st0.cpu().numpy())
+    assert s.host_device_status() in (0, 1)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
