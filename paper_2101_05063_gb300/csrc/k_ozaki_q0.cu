@@ -183,10 +183,6 @@ k_oz_gemm(int n, int ncol, OzLayout o, const __grid_constant__ CUtensorMap mapA,
     if (warp == 0) {
         // ---- producer: TMA of the 7 digit matrices of A and B per K slice
         if (lane == 0) {
-            // Q0's digits are read by the few blocks of one row tile at about
-            // the same time; X's digits by every row tile: keep those in L2
-            const uint64_t pol_a = tc::l2_policy_evict_first();
-            const uint64_t pol_b = tc::l2_policy_evict_last();
             for (int kb = 0; kb < nK && !abort_flag; ++kb) {
                 const int s = kb % STAGES;
                 if (kb >= STAGES && !tc::mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
@@ -195,8 +191,8 @@ k_oz_gemm(int n, int ncol, OzLayout o, const __grid_constant__ CUtensorMap mapA,
                 }
                 unsigned char* st = smem + s * kStageBytes;
                 tc::mbar_expect_tx(&full[s], kStageBytes);
-                tc::tma_load_3d_hint(st, &mapA, kb * BK, m0, 0, &full[s], pol_a);
-                tc::tma_load_3d_hint(st + kABytes, &mapB, kb * BK, n0, 0, &full[s], pol_b);
+                tc::tma_load_3d(st, &mapA, kb * BK, m0, 0, &full[s]);
+                tc::tma_load_3d(st + kABytes, &mapB, kb * BK, n0, 0, &full[s]);
                 last_kb[s] = kb;
             }
         }

@@ -53,28 +53,6 @@ __device__ inline void tma_load_3d(void* dst, const CUtensorMap* map, int x, int
         : "memory");
 }
 
-// the same with an L2 eviction priority (a policy from l2_policy_*)
-__device__ inline void tma_load_3d_hint(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                        uint64_t* bar, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;\n" ::"r"(
-            su32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(su32(bar)), "l"(policy)
-        : "memory");
-}
-// L2 policies: data read once (evict first) and data many blocks re-read
-// (evict last)
-__device__ inline uint64_t l2_policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
-    return p;
-}
-__device__ inline uint64_t l2_policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
-    return p;
-}
-
 __device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::); }
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::); }
