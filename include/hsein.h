@@ -387,8 +387,9 @@ hsein_status hsein_batch_solve(hsein_batch_t batch, void *dWork, size_t work_byt
 
 /*
  * Autotuner: times the batch (graph replays, CUDA events on `stream`) under
- * each configuration of a fixed candidate set (tile-height policies x shift
- * block widths x chain counts), keeps the fastest for later solves and
+ * the configurations of a fixed candidate set, one coordinate at a time
+ * (tile-height policies 0..2, then shift block widths {all, 512, 256, 128},
+ * then chain counts {4, 8, 16, 24, 32, 48}), keeps the fastest for later solves and
  * returns it in *chosen (may be NULL) and its time in *ms (may be NULL).
  * Synchronizes `stream`; the instances' outputs hold the last trial's results.
  */

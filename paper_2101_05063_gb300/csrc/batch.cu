@@ -227,8 +227,8 @@ void destroy(hsein_batch_s* b) {
 
 // the candidate set the autotuner searches (coordinate-wise, in this order)
 const int kPolicies[] = {0, 1, 2};
-const int kBlocks[] = {0, 256};
-const int kStreams[] = {8, 16, 32};
+const int kBlocks[] = {0, 512, 256, 128};
+const int kStreams[] = {4, 8, 16, 24, 32, 48};
 
 }  // namespace
 
@@ -371,7 +371,9 @@ hsein_status hsein_batch_autotune(hsein_batch_t b, void* dWork, size_t work_byte
     // coordinate search: tile-height policy, then shift blocks, then chains
     for (int dim = 0; dim < 3 && rc == HSEIN_OK; ++dim) {
         const int* vals = dim == 0 ? kPolicies : dim == 1 ? kBlocks : kStreams;
-        const int nv = dim == 0 ? 3 : dim == 1 ? 2 : 3;
+        const int nv = dim == 0 ? (int)(sizeof(kPolicies) / sizeof(int))
+                     : dim == 1 ? (int)(sizeof(kBlocks) / sizeof(int))
+                                : (int)(sizeof(kStreams) / sizeof(int));
         hsein_batch_config base = best;
         for (int i = 0; i < nv && rc == HSEIN_OK; ++i) {
             hsein_batch_config c = base;
