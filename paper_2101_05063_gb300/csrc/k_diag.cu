@@ -80,6 +80,13 @@ __device__ inline double group_max(double v) {
 }
 
 // LPS lanes per shift (32 / LPS shifts per warp), RPL rows per lane
+// -v by flipping the sign bit.  A negated double that feeds a select is
+// otherwise formed by an FP64 instruction, and on GB300 every FP64 warp
+// instruction of the sweep's per-step stream costs issue time
+__device__ inline double negd(double v) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
+}
+
 template <int LPS, int RPL, bool CPLX>
 __device__ void tile_group(const Layout& L, void* work, const double* __restrict__ Hs, int J,
                            int p0, int bt, int q, bool qok, int robust, int om, double* sm) {
@@ -233,10 +240,11 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
             const double ss = CPLX ? fma(vkr, vkr, fma(vki, vki, h2)) : fma(vkr, vkr, h2);
             const double rr = rsqrt(ss);
             double m1;
+            const double nhs = negd(hs);
             if (CPLX)
-                m1 = role == 0 ? vkr : role == 1 ? vki : role == 2 ? -hs : role == 3 ? xkr : xki;
+                m1 = role == 0 ? vkr : role == 1 ? vki : role == 2 ? nhs : role == 3 ? xkr : xki;
             else
-                m1 = role == 0 ? vkr : role == 1 ? -hs : xkr;
+                m1 = role == 0 ? vkr : role == 1 ? nhs : xkr;
             const double f1 = m1 * rr;
             double cr = __shfl_sync(kFull, f1, gbase);
             double ci = CPLX ? __shfl_sync(kFull, f1, gbase | 1) : 0.0;
@@ -248,7 +256,7 @@ __device__ void tile_group(const Layout& L, void* work, const double* __restrict
             if (CPLX) {
                 const double u0 = (role & 1) ? xki1 : xkr1;
                 const double v0 = role < 2 ? cr : s;
-                const double u1 = role == 0 ? xki1 : role == 1 ? -xkr1 : 0.0;
+                const double u1 = role == 0 ? xki1 : role == 1 ? negd(xkr1) : 0.0;
                 const double v1 = role < 2 ? ci : 0.0;
                 f2 = fma(u0, v0, u1 * v1);
             } else {

@@ -80,19 +80,38 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
     }
     __syncthreads();
     const int emax = s_emax;
-    // tile of row i and its consistency factor 2^(e_tile - e_max)
-    auto factor = [&](int i) {
-        int J = i < L.b0 ? 0 : 1 + (i - L.b0) / L.br;
-        return pow2(etile[(size_t)J * L.m + q] - emax);
-    };
     const int cs = (n + kThreads - 1) / kThreads;
     const int a0 = min(n, tid * cs), a1 = min(n, a0 + cs);
+    // the consistency factor 2^(e_tile - e_max) of the tile of each row, for
+    // rows a0, a0+1, ... in turn: the tile index is found once per pass and
+    // then advanced at tile boundaries
+    struct Factor {
+        int J, next;
+        double f;
+    };
+    auto factor_at = [&](int J) { return pow2(etile[(size_t)J * L.m + q] - emax); };
+    auto factor_start = [&]() {
+        Factor t;
+        t.J = a0 < L.b0 ? 0 : 1 + (a0 - L.b0) / L.br;
+        t.next = tile_start(L, t.J + 1);
+        t.f = t.J < L.N ? factor_at(t.J) : 1.0;
+        return t;
+    };
+    auto factor = [&](Factor& t, int i) {
+        if (i == t.next) {
+            ++t.J;
+            t.next += L.br;
+            t.f = factor_at(t.J);
+        }
+        return t.f;
+    };
     // scaled 2-norm of the consistently scaled column: the largest magnitude
     // as an integer maximum of bit patterns, then sum (v_i 2^-e)^2 with the
     // exact power-of-two scale 2^e of that maximum (no division per element)
     unsigned long long mb = 0;
+    Factor ft = factor_start();
     for (int i = a0; i < a1; ++i) {
-        const double f = factor(i);
+        const double f = factor(ft, i);
         mb = max(mb, abs_bits(xr[i] * f));
         if (CPLX) mb = max(mb, abs_bits(xi[i] * f));
     }
@@ -105,8 +124,9 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
     const int ne = norm_exp(mb);
     const double nsc = pow2(-ne);
     double ss = 0.0;
+    ft = factor_start();
     for (int i = a0; i < a1; ++i) {
-        const double g = factor(i) * nsc;
+        const double g = factor(ft, i) * nsc;
         const double t0 = xr[i] * g;
         ss = fma(t0, t0, ss);
         if (CPLX) {
@@ -147,8 +167,9 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
     const double inv = s_scale;
     // chunk map: tau_out = a tau_in + b over rows a0..a1-1
     Aff f{1.0, 0.0, 0.0};
+    ft = factor_start();
     for (int k = a0; k < a1; ++k) {
-        double g = factor(k) * inv;
+        double g = factor(ft, k) * inv;
         double yk_r = xr[k] * g, yk_i = CPLX ? xi[k] * g : 0.0;
         Aff step;
         if (k == 0) {
@@ -186,8 +207,9 @@ __device__ void finalize_shift(const Layout& L, void* work, int q, double* __res
                 __shfl_up_sync(0xffffffffu, inc.bi, 1)};
     if (lane > 0) ex = aff_then(ex, lanepre);
     double tr = ex.br, ti = ex.bi;  // tau entering row a0 (the map applied to 0)
+    ft = factor_start();
     for (int k = a0; k < a1; ++k) {
-        double g = factor(k) * inv;
+        double g = factor(ft, k) * inv;
         double yk_r = xr[k] * g, yk_i = CPLX ? xi[k] * g : 0.0;
         if (k == 0) {
             tr = yk_r;
