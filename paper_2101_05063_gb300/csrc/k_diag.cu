@@ -80,9 +80,10 @@ __device__ inline double group_max(double v) {
 }
 
 // LPS lanes per shift (32 / LPS shifts per warp), RPL rows per lane
-// -v by flipping the sign bit.  A negated double that feeds a select is
-// otherwise formed by an FP64 instruction, and on GB300 every FP64 warp
-// instruction of the sweep's per-step stream costs issue time
+// -v by flipping the sign bit (exact).  Used for the negated values that
+// feed the rotation's selects: the sweep's step measured shorter this way
+// than with the compiler's own negation (same FP64 instruction count, a
+// different schedule)
 __device__ inline double negd(double v) {
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
 }

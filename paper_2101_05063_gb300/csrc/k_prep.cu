@@ -131,12 +131,15 @@ __global__ void k_rowpart(Layout L, void* work, const double* __restrict__ H, in
     int j0, j1;
     chunk_range(L, c, &j0, &j1);
     if (j0 < i - 1) j0 = i - 1;  // entries below the subdiagonal are not read
+    // the finiteness and zero tests read the exponent and magnitude bits
+    // (integer operations; on GB300 an FP64 compare costs an FP64 pipe slot)
     double s = 0.0;
     bool finite = true, zero_sub = false;
     for (int j = j0; j < j1; ++j) {
-        double h = H[i + (size_t)j * ldh];
-        finite = finite && isfinite(h);
-        if (j == i - 1 && h == 0.0) zero_sub = true;
+        const double h = H[i + (size_t)j * ldh];
+        const unsigned long long m = abs_bits(h);
+        finite = finite && m < 0x7FF0000000000000ULL;
+        if (j == i - 1 && m == 0) zero_sub = true;
         s += fabs(h);
     }
     part[i + (size_t)c * L.n] = s;
@@ -223,7 +226,11 @@ __global__ void k_init(Layout L, void* work, const double* __restrict__ H, int l
         const double b0 = B ? B[i + (size_t)uc * ldb] : rho;
         X[i + (size_t)c * L.ldw] = b0;
         xm = max(xm, abs_bits(b0));
-        const double r0 = H[i + (size_t)(L.n - 1) * ldh] * hscale - (i == L.n - 1 ? lre : 0.0);
+        // h(i, n) prescaled (the factor is 1 unless ||H|| is huge), minus
+        // lambda' on row n
+        double r0 = H[i + (size_t)(L.n - 1) * ldh];
+        if (s != 0) r0 *= hscale;
+        if (i == L.n - 1) r0 -= lre;
         R[i + (size_t)c * L.ldw] = r0;
         rm = max(rm, abs_bits(r0));
         if (cplx) {
