@@ -73,6 +73,7 @@ void make_layout(Layout* L, int n, int mr, int mc, int br, int precision, int gi
     L->N = (n + br - 1) / br;
     L->b0 = n - (L->N - 1) * br;
     L->ldw = (n + 7) / 8 * 8;
+    L->lps_real = 16;  // set for the plan's GPU by hsein_plan
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t at = o;
@@ -229,6 +230,7 @@ hsein_status hsein_plan(hsein_plan_t* plan, int n, int m_real, int m_cplx,
         delete p;
         return HSEIN_ECUDA;
     }
+    p->L.lps_real = hsein::diag_lanes_real(p->L, p->num_sms);
     if (workspace_bytes) *workspace_bytes = p->L.total + restart_reserve(n);
     *plan = p;
     return HSEIN_OK;

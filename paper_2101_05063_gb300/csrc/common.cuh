@@ -67,6 +67,7 @@ struct Layout {
     int compact;  // 1: Givens rotations stored compactly (Stewart's scheme)
     int lu_slots;          // per-shift LU baseline: shifts factored at once
     size_t lu_slot_bytes;  // and the workspace of one (packed U, row maxima)
+    int lps_real;          // lanes per real shift in the diagonal-tile sweep (16 or 8)
 };
 
 // first row of tile J (tile 0 is the ragged top-left tile of height b0)
@@ -232,6 +233,8 @@ void launch_prepare(const Layout& L, void* work, const double* H, int ldh, const
                     const double* wi, const double* B, int ldb, int omega_log2, cudaStream_t s);
 void launch_diag(const Layout& L, void* work, int J, int robust, int omega_log2,
                  long long wait_limit, cudaStream_t s);
+// lanes per real shift for the sweep of this layout on a GPU with num_sms SMs
+int diag_lanes_real(const Layout& L, int num_sms);
 void launch_update(const Layout& L, void* work, const double* H, int ldh, int J, cudaStream_t s);
 // per-shift LU comparison baseline (method 2)
 size_t lu_slot_bytes(int n);

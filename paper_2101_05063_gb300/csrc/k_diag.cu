@@ -788,10 +788,19 @@ void launch_stage_tiles(const Layout& L, void* work, const double* H, int ldh, c
 }
 
 // lanes per shift: complex shifts take a whole warp, real shifts half of one
-// (the FP64 unit of an SM sub-partition serves one warp instruction at a time,
-// so fewer shifts per warp spread the sweep over more sub-partitions)
-constexpr int kLpsC = 32, kLpsR = 16;
-constexpr int kMaxGroups = 32 / kLpsR;
+// (the FP64 unit of an SM sub-partition serves one warp instruction at a
+// time, so fewer shifts per warp spread the sweep over more sub-partitions),
+// or a quarter of one when half-warps would give more warps than the GPU has
+// sub-partitions: two warps on one sub-partition take longer per step than
+// one warp with twice the shifts (n = 8192, 2048 real shifts: 18.9 -> 13.5 ms
+// per solve).  Four shifts per warp need tile heights up to 64 (eight rows
+// per lane).
+constexpr int kLpsC = 32;
+
+int diag_lanes_real(const Layout& L, int num_sms) {
+    const int warps_half = L.mc + (L.mr + 1) / 2;
+    return (L.br <= 64 && warps_half > 4 * num_sms) ? 8 : 16;
+}
 
 static int pow2_at_least(int v) {
     int p = 1;
@@ -799,28 +808,40 @@ static int pow2_at_least(int v) {
     return p;
 }
 
-template <int RC, int RR>
+template <int RC, int RR, int LPSR>
 static void launch_t(const Layout& L, void* work, int J, int robust, int om, int nbc, int grid,
                      size_t smem, long long wl, cudaStream_t s) {
-    k_diag<kLpsC, RC, kLpsR, RR><<<grid, 32, smem, s>>>(L, work, J, robust, om, nbc, wl);
+    k_diag<kLpsC, RC, LPSR, RR><<<grid, 32, smem, s>>>(L, work, J, robust, om, nbc, wl);
 }
 
-static size_t diag_smem(int br) {
-    return ((size_t)br * br + (size_t)kMaxGroups * 7 * br) * sizeof(double);
+// the staged tile, then 7 br doubles of scratch per shift group of a warp
+static size_t diag_smem(int br, int lpsr) {
+    return ((size_t)br * br + (size_t)(32 / lpsr) * 7 * br) * sizeof(double);
 }
 
 void launch_diag(const Layout& L, void* work, int J, int robust, int omega_log2,
                  long long wait_limit, cudaStream_t s) {
+    const int lpsr = L.lps_real;
     const int nbc = (L.mc + (32 / kLpsC) - 1) / (32 / kLpsC);
-    const int nbr = (L.mr + (32 / kLpsR) - 1) / (32 / kLpsR);
-    const size_t smem = diag_smem(L.br);
+    const int nbr = (L.mr + (32 / lpsr) - 1) / (32 / lpsr);
+    const size_t smem = diag_smem(L.br, lpsr);
     const int grid = nbc + nbr;
-    // rows per lane, rounded up to a power of two: complex br/32, real br/16
-    switch (pow2_at_least((L.br + kLpsR - 1) / kLpsR)) {
-        case 1: launch_t<1, 1>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
-        case 2: launch_t<1, 2>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
-        case 4: launch_t<2, 4>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
-        default: launch_t<4, 8>(L, work, J, robust, omega_log2, nbc, grid, smem, wait_limit, s); break;
+    const int om = omega_log2;
+    // rows per lane, rounded up to a power of two: complex br/32, real br/lpsr
+    if (lpsr == 8) {
+        switch (pow2_at_least((L.br + 7) / 8)) {
+            case 1: launch_t<1, 1, 8>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
+            case 2: launch_t<1, 2, 8>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
+            case 4: launch_t<1, 4, 8>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
+            default: launch_t<2, 8, 8>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
+        }
+        return;
+    }
+    switch (pow2_at_least((L.br + 15) / 16)) {
+        case 1: launch_t<1, 1, 16>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
+        case 2: launch_t<1, 2, 16>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
+        case 4: launch_t<2, 4, 16>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
+        default: launch_t<4, 8, 16>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
     }
 }
 
@@ -829,11 +850,19 @@ void launch_diag(const Layout& L, void* work, int J, int robust, int omega_log2,
 // largest tile height it serves (plans of different heights coexist)
 cudaError_t diag_configure(int br) {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    switch (pow2_at_least((br + kLpsR - 1) / kLpsR)) {
-        case 1: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 1>, a, (int)diag_smem(kLpsR));
-        case 2: return cudaFuncSetAttribute(k_diag<kLpsC, 1, kLpsR, 2>, a, (int)diag_smem(2 * kLpsR));
-        case 4: return cudaFuncSetAttribute(k_diag<kLpsC, 2, kLpsR, 4>, a, (int)diag_smem(4 * kLpsR));
-        default: return cudaFuncSetAttribute(k_diag<kLpsC, 4, kLpsR, 8>, a, (int)diag_smem(kMaxBr));
+    cudaError_t e = cudaSuccess;
+    switch (pow2_at_least((br + 15) / 16)) {
+        case 1: e = cudaFuncSetAttribute(k_diag<kLpsC, 1, 16, 1>, a, (int)diag_smem(16, 16)); break;
+        case 2: e = cudaFuncSetAttribute(k_diag<kLpsC, 1, 16, 2>, a, (int)diag_smem(32, 16)); break;
+        case 4: e = cudaFuncSetAttribute(k_diag<kLpsC, 2, 16, 4>, a, (int)diag_smem(64, 16)); break;
+        default: e = cudaFuncSetAttribute(k_diag<kLpsC, 4, 16, 8>, a, (int)diag_smem(kMaxBr, 16)); break;
+    }
+    if (e != cudaSuccess || br > 64) return e;
+    switch (pow2_at_least((br + 7) / 8)) {
+        case 1: return cudaFuncSetAttribute(k_diag<kLpsC, 1, 8, 1>, a, (int)diag_smem(8, 8));
+        case 2: return cudaFuncSetAttribute(k_diag<kLpsC, 1, 8, 2>, a, (int)diag_smem(16, 8));
+        case 4: return cudaFuncSetAttribute(k_diag<kLpsC, 1, 8, 4>, a, (int)diag_smem(32, 8));
+        default: return cudaFuncSetAttribute(k_diag<kLpsC, 2, 8, 8>, a, (int)diag_smem(64, 8));
     }
 }
 

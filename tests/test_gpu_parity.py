@@ -112,6 +112,34 @@ def test_small_instances_match_oracle(n, mr, mc, br, seed):
     compare(H, wr, wi, Xg, sg, Xo, so, eigs)
 
 
+@pytest.mark.parametrize("precision,br", [(0, 32), (1, 64)])
+def test_many_real_shifts_four_per_warp(precision, br):
+    """More real shifts than the GPU has SM sub-partitions for at two shifts
+    per warp: the sweep packs four real shifts per warp.  Statuses and
+    directions of a seeded sample of shifts against the oracle, and the
+    residual of every converged real column."""
+    n, mr, mc = 1536, 1300, 20
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert mc + (mr + 1) // 2 > 4 * sms  # the packed layout is the one used
+    inst = hi.small_instance(n, mr, mc, 61)
+    Xg, sg, _ = run_gpu(inst.H, inst.wr, inst.wi, inst.B, br=br, precision=precision)
+    offs = hi.column_offsets(inst.wi)
+    pick = np.sort(np.argsort(hi.uniform(62, 0, mr + mc), kind="stable")[:48])
+    pick = np.union1d(pick, np.nonzero(inst.wi)[0][:4])  # complex shifts too
+    cols = np.concatenate([np.arange(offs[l], offs[l + 1]) for l in pick])
+    Xo, so = oracle.hsein(inst.H, inst.wr[pick], inst.wi[pick], inst.B[:, cols])
+    compare(inst.H, inst.wr[pick], inst.wi[pick], Xg[:, cols], sg[pick], Xo, so, inst.eigs)
+    real = np.nonzero((inst.wi == 0) & (sg == 0))[0]
+    rc = np.array([offs[l] for l in real])
+    Hd = to_dev(inst.H)
+    Xd = to_dev(Xg[:, rc])
+    lam = to_dev(inst.wr[real])
+    R = Hd @ Xd - Xd * lam
+    r = (R.abs().sum(0) / (Hd.abs().sum(0).max() * Xd.abs().sum(0))).max().item()
+    assert r <= 100 * n * EPS, r / (n * EPS)
+    assert len(real) >= 0.9 * mr
+
+
 @pytest.mark.parametrize("br", [16, 64])
 def test_default_starting_vector(br):
     inst = hi.small_instance(150, 10, 6, 21)
