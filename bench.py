@@ -664,6 +664,32 @@ def residual_max_device(torch, dH, X, wr, wi, status, n):
     return worst / (n * EPS)
 
 
+def timed_steps(torch, stream, step, steps):
+    """Run `steps` steps between CUDA events on `stream` (one event between
+    consecutive steps); the per-step times in ms."""
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for i in range(steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    return [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+
+
+def profiled_steps(torch, hs, solver, stream, step, steps):
+    """The same steps again with a CUDA event pair around every launch of the
+    solver (the phase breakdown and the per-launch kernel times): the events
+    themselves lengthen a step, so the throughput and latency come from the
+    plain region and this one supplies the per-kernel figures.  Returns the
+    phases and this region's ms per step."""
+    hs.hsein_plan_set_profiling(solver.plan, True)
+    hs.hsein_plan_profile(solver.plan, reset=True)
+    per = timed_steps(torch, stream, step, steps)
+    prof = hs.hsein_plan_profile(solver.plan, reset=True)
+    hs.hsein_plan_set_profiling(solver.plan, False)
+    return prof, float(sum(per)) / steps
+
+
 def measure_instance(torch, hs, inst, precision, steps, warmup, br=64, keep=False):
     """Time `steps` steps (hsein_solve + hsein_backtransform) of one instance
     in one precision mode, inputs resident in HBM; per-step latency, phases,
@@ -687,18 +713,10 @@ def measure_instance(torch, hs, inst, precision, steps, warmup, br=64, keep=Fals
     torch.cuda.synchronize()
     if solver.device_status() < 0:
         raise RuntimeError("device status %d" % solver.device_status())
-    hs.hsein_plan_set_profiling(solver.plan, True)
-    hs.hsein_plan_profile(solver.plan, reset=True)
     stream = torch.cuda.current_stream()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    evs[0].record(stream)
-    for i in range(steps):
-        step()
-        evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    prof = hs.hsein_plan_profile(solver.plan, reset=True)
-    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    per = timed_steps(torch, stream, step, steps)
     ms = float(sum(per)) / steps
+    prof, ms_events = profiled_steps(torch, hs, solver, stream, step, steps)
     sh = status.cpu().numpy()
     offs = hi.column_offsets(inst.wi)
     conv = int(sum(offs[l + 1] - offs[l] for l in range(inst.m) if sh[l] == 0))
@@ -709,7 +727,8 @@ def measure_instance(torch, hs, inst, precision, steps, warmup, br=64, keep=Fals
                                                           status, n),
            "not_converged": int((sh != 0).sum()), "converged_columns": conv,
            "phases": {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
-                      for k, v in prof.items()}}
+                      for k, v in prof.items()},
+           "ms_per_step_with_launch_events": ms_events}
     host = (X.cpu().numpy(), sh) if keep else None
     del solver, dH, dQ, dB, X, Z
     torch.cuda.empty_cache()
@@ -847,24 +866,18 @@ def main():
         sampler = ClockSampler(torch.cuda.current_device()) if (rank == 0 and sample_clocks) else None
         if sampler:
             sampler.start()
-        hs.hsein_plan_set_profiling(solver.plan, True)
-        hs.hsein_plan_profile(solver.plan, reset=True)
         barrier(world)
         torch.cuda.synchronize()
         # one event between consecutive steps: per-step latency and the total
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
-        evs[0].record(stream)
-        for i in range(nsteps):
-            step()
-            evs[i + 1].record(stream)
-        torch.cuda.synchronize()
+        per_step = timed_steps(torch, stream, step, nsteps)
         barrier(world)
-        ms = evs[0].elapsed_time(evs[-1])
-        per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(nsteps)]
+        ms = float(sum(per_step))
         lat = {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                "unit": "ms", "of": "%d steps" % nsteps}
-        prof = hs.hsein_plan_profile(solver.plan, reset=True)
-        hs.hsein_plan_set_profiling(solver.plan, False)
+        # the per-launch kernel times (phases, roofline) from a second timed
+        # region of the same steps
+        prof, ms_ev = profiled_steps(torch, hs, solver, stream, step, nsteps)
+        lat["ms_per_step_with_launch_events"] = ms_ev
         clocks = sampler.stop() if sampler else None
         return solver, step, max_over_ranks(ms, world), prof, worst, sh, clocks, lat
 
@@ -1066,7 +1079,11 @@ def main():
                      "algorithmic_flops_per_launch": df / dlaunch,
                      "flop_count": "5 n b_r per column per solve (per launch: 5 b_r^2 ncol)",
                      "frac_of_probe": achieved_d / probe,
-                     "frac_of_bf16_derived": achieved_d / bf_d},
+                     "frac_of_bf16_derived": achieved_d / bf_d,
+                     "timed": "average CUDA-event duration of the kernel's launches "
+                              "(an event pair around each, on the launching stream) "
+                              "over a second timed region of the same %d steps"
+                              % args.steps},
         "fp64_peak": fp64_peak_info,
         "tensor": tensor,
         "phases": per_phase(prof_sp),
