@@ -714,15 +714,21 @@ def measure_instance(torch, hs, inst, precision, steps, warmup, br=64, keep=Fals
     if solver.device_status() < 0:
         raise RuntimeError("device status %d" % solver.device_status())
     stream = torch.cuda.current_stream()
-    per = timed_steps(torch, stream, step, steps)
+    graph = solver.graph(dH, dwr, dwi, dB, dQ, X=X, status=status, Z=Z)
+    graph.launch()
+    per = timed_steps(torch, stream, graph.launch, steps)
     ms = float(sum(per)) / steps
+    ms_eager = float(sum(timed_steps(torch, stream, step, steps))) / steps
     prof, ms_events = profiled_steps(torch, hs, solver, stream, step, steps)
+    del graph
     sh = status.cpu().numpy()
     offs = hi.column_offsets(inst.wi)
     conv = int(sum(offs[l + 1] - offs[l] for l in range(inst.m) if sh[l] == 0))
     out = {"value": conv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
            "latency": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
-                       "unit": "ms", "of": "%d steps" % steps},
+                       "unit": "ms", "of": "%d steps" % steps,
+                       "launch": "one CUDA graph per step"},
+           "ms_per_step_eager": ms_eager,
            "residual_max_over_n_eps": residual_max_device(torch, dH, X, inst.wr, inst.wi,
                                                           status, n),
            "not_converged": int((sh != 0).sum()), "converged_columns": conv,
@@ -866,18 +872,25 @@ def main():
         sampler = ClockSampler(torch.cuda.current_device()) if (rank == 0 and sample_clocks) else None
         if sampler:
             sampler.start()
+        # the same step captured as one CUDA graph (hsein_graph_create): the
+        # throughput and latency are timed through it
+        graph = solver.graph(dH, dwr, dwi, dB, dQ, X=X, status=status, Z=Z)
+        graph.launch()
         barrier(world)
         torch.cuda.synchronize()
         # one event between consecutive steps: per-step latency and the total
-        per_step = timed_steps(torch, stream, step, nsteps)
+        per_step = timed_steps(torch, stream, graph.launch, nsteps)
         barrier(world)
         ms = float(sum(per_step))
         lat = {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
-               "unit": "ms", "of": "%d steps" % nsteps}
-        # the per-launch kernel times (phases, roofline) from a second timed
-        # region of the same steps
+               "unit": "ms", "of": "%d steps" % nsteps, "launch": "one CUDA graph per step"}
+        # the same steps launched kernel by kernel from the host
+        lat["ms_per_step_eager"] = float(sum(timed_steps(torch, stream, step, nsteps))) / nsteps
+        # the per-launch kernel times (phases, roofline) from a timed region
+        # of the same steps with an event pair around every launch
         prof, ms_ev = profiled_steps(torch, hs, solver, stream, step, nsteps)
         lat["ms_per_step_with_launch_events"] = ms_ev
+        del graph
         clocks = sampler.stop() if sampler else None
         return solver, step, max_over_ranks(ms, world), prof, worst, sh, clocks, lat
 

@@ -12,6 +12,8 @@ is no CPU fallback: if the library cannot be loaded, every call raises.
     X, status = solver.solve(H, wr, wi, B)            # unit eigenvectors of H
     Z = solver.backtransform(Q0, X)                   # eigenvectors of A
     solver.solve_host(hH, hwr, hwi, hB, hQ0, hZ, hst) # the same from pinned host buffers
+    step = solver.graph(H, wr, wi, B, Q0)             # solve + Z = Q0 X as one CUDA graph
+    step.launch()                                     # results in step.X, step.status, step.Z
 
 Options of Solver: precision=1 (split-precision products on the BF16 tensor
 cores, the fast mode), givens=1 (compact rotation storage), method=1 / 2 (the
@@ -40,7 +42,8 @@ __all__ = [
     "hsein_plan_info", "hsein_plan_destroy",
     "hsein_status_string", "hsein_plan_set_profiling", "hsein_plan_profile", "Solver",
     "STATUS", "PHASES", "hsein_fp64_rate", "fp64_rate", "hsein_host_workspace",
-    "hsein_solve_host",
+    "hsein_solve_host", "StepGraph", "hsein_graph_create", "hsein_graph_launch",
+    "hsein_graph_destroy",
 ]
 
 STATUS = {0: "HSEIN_OK", -1: "HSEIN_EARG", -2: "HSEIN_ENOMEM", -3: "HSEIN_ENOTUNREDUCED",
@@ -112,6 +115,13 @@ def load(build_if_missing=True):
     lib.hsein_solve_noalloc.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, vp]
     lib.hsein_backtransform.restype = ctypes.c_int
     lib.hsein_backtransform.argtypes = [vp, dp, ip, dp, ip, dp, ip, vp, sz, vp]
+    lib.hsein_graph_create.restype = ctypes.c_int
+    lib.hsein_graph_create.argtypes = [vp, dp, ip, dp, dp, dp, ip, dp, ip, dp, dp, ip, dp, ip,
+                                       vp, sz, ctypes.POINTER(vp)]
+    lib.hsein_graph_launch.restype = ctypes.c_int
+    lib.hsein_graph_launch.argtypes = [vp, vp]
+    lib.hsein_graph_destroy.restype = ctypes.c_int
+    lib.hsein_graph_destroy.argtypes = [vp]
     lib.hsein_plan_sync_status.restype = ctypes.c_int
     lib.hsein_plan_sync_status.argtypes = [vp, vp, vp]
     lib.hsein_margins.restype = ctypes.c_int
@@ -197,6 +207,26 @@ def hsein_solve(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, dWork, work_
     """Device pointers are integers (e.g. tensor.data_ptr()); dB may be 0."""
     return load().hsein_solve(plan, dH, ldh, dWr, dWi, dB or None, ldb, dX, ldx, dStatus, dWork,
                               work_bytes, stream or None)
+
+
+def hsein_graph_create(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, dQ0, ldq, dZ, ldz,
+                       dWork, work_bytes):
+    """One step (hsein_solve, then hsein_backtransform when dQ0 is not 0)
+    captured as a CUDA graph on these device buffers; returns (status,
+    handle)."""
+    g = ctypes.c_void_p()
+    rc = load().hsein_graph_create(plan, dH, ldh, dWr, dWi, dB or None, ldb, dX, ldx, dStatus,
+                                   dQ0 or None, ldq, dZ or None, ldz, dWork, work_bytes,
+                                   ctypes.byref(g))
+    return rc, g
+
+
+def hsein_graph_launch(graph, stream):
+    return load().hsein_graph_launch(graph, stream or None)
+
+
+def hsein_graph_destroy(graph):
+    return load().hsein_graph_destroy(graph)
 
 
 def hsein_solve_noalloc(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, stream):
@@ -602,6 +632,55 @@ class Solver:
                                  self._stream())
         _check(rc, "hsein_backtransform")
         return Z
+
+    def graph(self, H, wr, wi, B=None, Q0=None, X=None, status=None, Z=None):
+        """One step (solve, then Z = Q0 X when Q0 is given) captured as a CUDA
+        graph on these buffers (hsein_graph_create); StepGraph.launch() runs
+        it on the current stream.  The tensors are used in place (inputs that
+        are already column-major float64 are not copied): refresh their
+        contents between launches."""
+        torch = self.torch
+        H = _colmajor(H, torch)
+        wr = wr.to(torch.float64).contiguous()
+        wi = wi.to(torch.float64).contiguous()
+        if B is not None:
+            B = _colmajor(B, torch)
+        if X is None:
+            X = torch.empty((self.ncol, self.n), dtype=torch.float64, device=self.device).t()
+        if status is None:
+            status = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        if Q0 is not None:
+            Q0 = _colmajor(Q0, torch)
+            if Z is None:
+                Z = torch.empty((self.ncol, self.n), dtype=torch.float64, device=self.device).t()
+        with torch.cuda.device(self.device):
+            rc, g = hsein_graph_create(
+                self.plan, H.data_ptr(), _ld(H), wr.data_ptr(), wi.data_ptr(),
+                B.data_ptr() if B is not None else 0, _ld(B) if B is not None else self.n,
+                X.data_ptr(), _ld(X), status.data_ptr(),
+                Q0.data_ptr() if Q0 is not None else 0, _ld(Q0) if Q0 is not None else self.n,
+                Z.data_ptr() if Z is not None else 0, _ld(Z) if Z is not None else self.n,
+                self.work.data_ptr(), self.work_bytes)
+        _check(rc, "hsein_graph_create")
+        return StepGraph(self, g, (H, wr, wi, B, Q0), X, status, Z)
+
+
+class StepGraph:
+    """A captured step of a Solver (Solver.graph); X, status and Z are its
+    outputs, valid once the launching stream has completed."""
+
+    def __init__(self, solver, handle, inputs, X, status, Z):
+        self.solver, self.handle, self._inputs = solver, handle, inputs
+        self.X, self.status, self.Z = X, status, Z
+
+    def launch(self):
+        _check(hsein_graph_launch(self.handle, self.solver._stream()), "hsein_graph_launch")
+
+    def __del__(self):
+        handle = getattr(self, "handle", None)
+        if handle is not None and _lib is not None:
+            _lib.hsein_graph_destroy(handle)
+            self.handle = None
 
 
 class Batch:

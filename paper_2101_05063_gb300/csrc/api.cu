@@ -50,6 +50,12 @@ struct hsein_plan_s {
     cudaEvent_t ev_q0 = nullptr, ev_done = nullptr;
 };
 
+// a captured step (hsein_graph_create)
+struct hsein_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -607,6 +613,66 @@ hsein_status hsein_plan_profile(hsein_plan_t plan, double* ms, int* launches, in
         plan->used = 0;
         plan->rec_phase.clear();
     }
+    return HSEIN_OK;
+}
+
+hsein_status hsein_graph_create(hsein_plan_t plan, const double* dH, int ldh, const double* dWr,
+                                const double* dWi, const double* dB, int ldb, double* dX, int ldx,
+                                int* dStatus, const double* dQ0, int ldq, double* dZ, int ldz,
+                                void* dWork, size_t work_bytes, hsein_graph_t* graph) {
+    if (!graph) return HSEIN_EARG;
+    *graph = nullptr;
+    if (!plan || (dQ0 && !dZ)) return HSEIN_EARG;
+    // a capture stream of its own (the legacy default stream cannot be
+    // captured); thread-local mode, so other threads' CUDA calls meanwhile
+    // do not invalidate the capture
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HSEIN_ECUDA;
+    const int profiling = plan->profiling;
+    plan->profiling = 0;
+    hsein_status rc = HSEIN_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = HSEIN_ECUDA;
+    } else {
+        rc = hsein_solve(plan, dH, ldh, dWr, dWi, dB, ldb, dX, ldx, dStatus, dWork, work_bytes, cs);
+        if (rc == HSEIN_OK && dQ0)
+            rc = hsein_backtransform(plan, dQ0, ldq, dX, ldx, dZ, ldz, dWork, work_bytes, cs);
+        if (cudaStreamEndCapture(cs, &g) != cudaSuccess && rc == HSEIN_OK) rc = HSEIN_ECUDA;
+    }
+    plan->profiling = profiling;
+    hsein_graph_s* h = nullptr;
+    if (rc == HSEIN_OK) {
+        h = new (std::nothrow) hsein_graph_s;
+        if (!h) rc = HSEIN_ENOMEM;
+        else if (cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess) rc = HSEIN_ECUDA;
+    }
+    if (rc != HSEIN_OK) {
+        delete h;
+        h = nullptr;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    } else {
+        h->graph = g;
+    }
+    cudaStreamDestroy(cs);
+    *graph = h;
+    return rc;
+}
+
+hsein_status hsein_graph_launch(hsein_graph_t graph, void* stream) {
+    if (!graph || !graph->exec) return HSEIN_EARG;
+    return cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? HSEIN_OK
+               : HSEIN_ECUDA;
+}
+
+hsein_status hsein_graph_destroy(hsein_graph_t graph) {
+    if (graph) {
+        if (graph->exec) cudaGraphExecDestroy(graph->exec);
+        if (graph->graph) cudaGraphDestroy(graph->graph);
+    }
+    delete graph;
     return HSEIN_OK;
 }
 

@@ -394,6 +394,59 @@ def test_split_precision_bad_system_h2(n, om):
     assert residual(H, 2.0, Xg[:, 0]) <= 100 * n * EPS
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_graph_matches_the_calls(precision):
+    """hsein_graph_create / hsein_graph_launch: the captured step gives the
+    results of hsein_solve + hsein_backtransform bitwise, at every launch, and
+    follows new contents of its input buffers; the solve-only graph too."""
+    inst = hi.small_instance(300, 20, 10, 71)
+    H, wr, wi, B, Q0 = (to_dev(inst.H), to_dev(inst.wr), to_dev(inst.wi), to_dev(inst.B),
+                        to_dev(inst.Q0))
+    s = hs.Solver(inst.n, inst.m_real, inst.m_cplx, precision=precision)
+    X0, st0 = s.solve(H, wr, wi, B)
+    Z0 = s.backtransform(Q0, X0)
+    step = s.graph(H, wr, wi, B, Q0)
+    for _ in range(2):
+        step.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(step.status, st0)
+        assert torch.equal(step.X, X0)
+        assert torch.equal(step.Z, Z0)
+    # new starting vectors in the same buffer
+    B.copy_(to_dev(np.roll(inst.B, 7, axis=0)))
+    X1, st1 = s.solve(H, wr, wi, B)
+    Z1 = s.backtransform(Q0, X1)
+    step.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(step.status, st1) and torch.equal(step.X, X1) and torch.equal(step.Z, Z1)
+    assert not torch.equal(X1, X0)
+    # the solve alone, default starting vector
+    Xd, std = s.solve(H, wr, wi, None)
+    solve_only = s.graph(H, wr, wi)
+    solve_only.launch()
+    torch.cuda.synchronize()
+    assert solve_only.Z is None
+    assert torch.equal(solve_only.status, std) and torch.equal(solve_only.X, Xd)
+    Xo, so = oracle.hsein(inst.H, inst.wr, inst.wi, None)
+    compare(inst.H, inst.wr, inst.wi, solve_only.X.cpu().numpy(), solve_only.status.cpu().numpy(),
+            Xo, so, inst.eigs)
+
+
+def test_step_graph_rejects_bad_arguments():
+    inst = hi.small_instance(64, 3, 1, 72)
+    s = hs.Solver(inst.n, inst.m_real, inst.m_cplx)
+    H, wr, wi = to_dev(inst.H), to_dev(inst.wr), to_dev(inst.wi)
+    with pytest.raises(hs.HseinError) as e:
+        s.graph(H, wr, wi, None, to_dev(inst.Q0), Z=torch.empty(0, dtype=torch.float64,
+                                                                device="cuda").reshape(0, 0))
+    assert e.value.code == -1
+    X = torch.empty((inst.ncol, inst.n), dtype=torch.float64, device="cuda").t()
+    rc, g = hs.hsein_graph_create(s.plan, H.data_ptr(), 10, wr.data_ptr(), wi.data_ptr(), 0,
+                                  inst.n, X.data_ptr(), inst.n, 0, 0, inst.n, 0, inst.n,
+                                  s.work.data_ptr(), s.work_bytes)
+    assert rc == -1 and not g.value  # ldh < n; no graph is left behind
+
+
 def test_solve_host_matches_device_path():
     # the end-to-end call from host buffers (hsein_solve_host) gives the
     # device path's results bit for bit (same kernels on the same inputs),
