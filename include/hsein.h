@@ -185,8 +185,11 @@ hsein_status hsein_backtransform(hsein_plan_t plan, const double *dQ0, int ldq,
  * (ldq >= n), hZ n x ncol output (ldz >= n), hStatus m output; pinned host
  * memory lets the copies run asynchronously.  dWork: device memory of
  * hsein_host_workspace bytes (the solve's workspace followed by the device
- * copies of the operands), 256-byte aligned.  Stream-ordered: hZ and
- * hStatus are valid once `stream` has completed.  Device errors as for
+ * copies of the operands), 256-byte aligned.  The solve on the device
+ * copies runs as a CUDA graph (hsein_graph_create), captured at the first
+ * call with this dWork and starting-vector choice and kept by the plan; while
+ * the plan records per-launch profiling it is launched kernel by kernel.
+ * Stream-ordered: hZ and hStatus are valid once `stream` has completed.  Device errors as for
  * hsein_solve (hsein_plan_sync_status on dWork).  The paper has no
  * counterpart: an interface convenience.
  */

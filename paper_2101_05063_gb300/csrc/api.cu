@@ -48,6 +48,11 @@ struct hsein_plan_s {
     // order it after the previous call's backtransform and before this one's
     cudaStream_t side = nullptr;
     cudaEvent_t ev_q0 = nullptr, ev_done = nullptr;
+    // hsein_solve_host: the solve on the device copies captured as a graph,
+    // for the workspace and starting-vector choice it was captured with
+    hsein_graph_s* host_graph = nullptr;
+    const void* host_graph_work = nullptr;
+    bool host_graph_b = false;
 };
 
 // a captured step (hsein_graph_create)
@@ -548,8 +553,26 @@ hsein_status hsein_solve_host(hsein_plan_t plan, const double* hH, int ldh, cons
                                  cudaMemcpyHostToDevice, plan->side) == cudaSuccess;
     ok = ok && cudaEventRecord(plan->ev_q0, plan->side) == cudaSuccess;
     if (!ok) return HSEIN_ECUDA;
-    hsein_status rc = hsein_solve(plan, dH, (int)n, dWr, dWi, hB ? dB : nullptr, (int)n, dX,
-                                  (int)n, dSt, dWork, L.total, stream);
+    // the solve on the device copies: as a graph captured at the first call
+    // with this workspace (one launch instead of one per kernel), or launch
+    // by launch while the plan records per-launch profiling events
+    hsein_status rc = HSEIN_OK;
+    if (plan->profiling) {
+        rc = hsein_solve(plan, dH, (int)n, dWr, dWi, hB ? dB : nullptr, (int)n, dX, (int)n, dSt,
+                         dWork, L.total, stream);
+    } else {
+        if (!plan->host_graph || plan->host_graph_work != dWork ||
+            plan->host_graph_b != (hB != nullptr)) {
+            hsein_graph_destroy(plan->host_graph);
+            plan->host_graph = nullptr;
+            rc = hsein_graph_create(plan, dH, (int)n, dWr, dWi, hB ? dB : nullptr, (int)n, dX,
+                                    (int)n, dSt, nullptr, 0, nullptr, 0, dWork, L.total,
+                                    &plan->host_graph);
+            plan->host_graph_work = dWork;
+            plan->host_graph_b = hB != nullptr;
+        }
+        if (rc == HSEIN_OK) rc = hsein_graph_launch(plan->host_graph, stream);
+    }
     if (rc != HSEIN_OK) return rc;
     if (cudaStreamWaitEvent(s, plan->ev_q0, 0) != cudaSuccess) return HSEIN_ECUDA;
     rc = hsein_backtransform(plan, dQ, (int)n, dX, (int)n, dZ, (int)n, dWork, L.total, stream);
@@ -682,6 +705,7 @@ hsein_status hsein_plan_destroy(hsein_plan_t plan) {
         if (plan->ev_q0) cudaEventDestroy(plan->ev_q0);
         if (plan->ev_done) cudaEventDestroy(plan->ev_done);
         if (plan->side) cudaStreamDestroy(plan->side);
+        hsein_graph_destroy(plan->host_graph);
     }
     delete plan;
     return HSEIN_OK;
