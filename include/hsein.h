@@ -207,7 +207,7 @@ hsein_status hsein_solve_host(hsein_plan_t plan, const double *hH, int ldh,
  * that graph on `stream`: the same kernels in the same order with the same
  * results as the two calls, without a host launch per kernel, which at
  * n = 4096 leaves the GPU idle between the sweep and update launches of
- * every tile column (10.42 -> 10.13 ms per step, measured).
+ * every tile column (10.41 -> 10.07 ms per step, measured).
  *   Arguments as for hsein_solve and hsein_backtransform (dZ, ldz may be
  *   NULL, 0 when dQ0 is NULL).  The buffers are used in place at every
  *   launch; refresh their contents between launches, do not free them
