@@ -81,3 +81,15 @@ def test_solve_rejects_null_plan_and_pointers(lib):
     assert lib.hsein_solve(None, None, 0, None, None, None, 0, None, 0, None, None, 0, None) == -1
     assert lib.hsein_backtransform(None, None, 0, None, 0, None, 0, None, 0, None) == -1
     assert lib.hsein_plan_destroy(None) == 0
+
+
+def test_graph_entry_points_reject_null_arguments(lib):
+    import ctypes
+    g = ctypes.c_void_p(1)
+    assert lib.hsein_graph_create(None, None, 0, None, None, None, 0, None, 0, None, None, 0,
+                                  None, 0, None, 0, ctypes.byref(g)) == -1
+    assert not g.value  # no handle on failure
+    assert lib.hsein_graph_create(None, None, 0, None, None, None, 0, None, 0, None, None, 0,
+                                  None, 0, None, 0, None) == -1
+    assert lib.hsein_graph_launch(None, None) == -1
+    assert lib.hsein_graph_destroy(None) == 0
