@@ -787,17 +787,19 @@ void launch_stage_tiles(const Layout& L, void* work, const double* H, int ldh, c
     k_stage_tiles<<<L.N, 256, 0, s>>>(L, work, H, ldh);
 }
 
-// lanes per shift: complex shifts take a whole warp, real shifts half of one
-// (the FP64 unit of an SM sub-partition serves one warp instruction at a
-// time, so fewer shifts per warp spread the sweep over more sub-partitions),
-// or a quarter of one when half-warps would give more warps than the GPU has
-// sub-partitions: two warps on one sub-partition take longer per step than
-// one warp with twice the shifts (n = 8192, 2048 real shifts: 18.9 -> 13.5 ms
-// per solve).  Four shifts per warp need tile heights up to 64 (eight rows
-// per lane).
+// lanes per shift: complex shifts take a whole warp; real shifts take a whole
+// warp too while one warp per shift fits on the GPU's SM sub-partitions (a
+// warp's step is bound by its own FP64 issue, so fewer shifts per warp give
+// shorter steps: n = 512, 64 shifts, 0.71 -> 0.61 ms per step), half of one
+// otherwise, or a quarter of one when half-warps would give more warps than
+// the GPU has sub-partitions: two warps on one sub-partition take longer per
+// step than one warp with twice the shifts (n = 8192, 2048 real shifts:
+// 18.9 -> 13.5 ms per solve).  One or four shifts per warp need tile heights
+// up to 64.
 constexpr int kLpsC = 32;
 
 int diag_lanes_real(const Layout& L, int num_sms) {
+    if (L.br <= 64 && L.mc + L.mr <= 4 * num_sms) return 32;
     const int warps_half = L.mc + (L.mr + 1) / 2;
     return (L.br <= 64 && warps_half > 4 * num_sms) ? 8 : 16;
 }
@@ -828,6 +830,11 @@ void launch_diag(const Layout& L, void* work, int J, int robust, int omega_log2,
     const int grid = nbc + nbr;
     const int om = omega_log2;
     // rows per lane, rounded up to a power of two: complex br/32, real br/lpsr
+    if (lpsr == 32) {
+        if (L.br <= 32) launch_t<1, 1, 32>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s);
+        else launch_t<2, 2, 32>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s);
+        return;
+    }
     if (lpsr == 8) {
         switch (pow2_at_least((L.br + 7) / 8)) {
             case 1: launch_t<1, 1, 8>(L, work, J, robust, om, nbc, grid, smem, wait_limit, s); break;
@@ -858,6 +865,9 @@ cudaError_t diag_configure(int br) {
         default: e = cudaFuncSetAttribute(k_diag<kLpsC, 4, 16, 8>, a, (int)diag_smem(kMaxBr, 16)); break;
     }
     if (e != cudaSuccess || br > 64) return e;
+    e = br <= 32 ? cudaFuncSetAttribute(k_diag<kLpsC, 1, 32, 1>, a, (int)diag_smem(32, 32))
+                 : cudaFuncSetAttribute(k_diag<kLpsC, 2, 32, 2>, a, (int)diag_smem(64, 32));
+    if (e != cudaSuccess) return e;
     switch (pow2_at_least((br + 7) / 8)) {
         case 1: return cudaFuncSetAttribute(k_diag<kLpsC, 1, 8, 1>, a, (int)diag_smem(8, 8));
         case 2: return cudaFuncSetAttribute(k_diag<kLpsC, 1, 8, 2>, a, (int)diag_smem(16, 8));
